@@ -1,0 +1,394 @@
+"""Benchmark: min-max NUFFT forward + adjoint throughput on GB300.
+
+One step = y = A x (scale+pad+FFT, interpolation) then x' = A^H y (gridding,
+inverse FFT + crop + rescale) on one batch of synthetic input: the operator
+pair of Section 2.1 (Eq. 1) and Section 2.1.4 (Eq. 2).  Metric: non-uniform
+points per second (M points per forward+adjoint pair), inputs resident in
+HBM, device-timed with CUDA events per step, L2 flushed between steps.
+
+Workload (default): 2D, 256x256 image, 512x512 grid, J = 6x6, golden-angle
+radial 403 spokes x 512 samples (206,336 points).  The 3D kooshball (128^3
+image, 256^3 grid, J = 6^3, 2,097,152 points) is measured in the same run and
+reported under "also".
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank runs an independent replica of the workload
+(the operator has no data-parallel exchange); time is the max over ranks and
+the value counts the points of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "NUFFT fwd+adj nonuniform pts/s (2D 256^2, 3D 128^3); % HBM roofline vs plain"
+UNIT = "points/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ------------------------------------------------------------------ helpers (host logic, tested on CPU)
+
+def algorithmic_bytes(spec: dict) -> dict:
+    """Minimum bytes each stage must move (complex64 data, int32 offsets)."""
+    d, M = spec["d"], spec["M"]
+    Nprod = int(np.prod(spec["Nd"]))
+    Kprod = int(np.prod(spec["Kd"]))
+    point = 4 * d + 8 * int(sum(spec["Jd"])) + 8          # first neighbours + coefficients + sample
+    return {
+        "scale_pad_fft": 8 * Nprod + 8 * Kprod,             # image read once, grid written once
+        "interp": 8 * Kprod + M * point,
+        "gridding": 8 * Kprod + M * point,
+        "ifft_crop_rescale": 8 * Kprod + 8 * Nprod,
+    }
+
+
+def launches_per_step(spec: dict, nchunks: int) -> int:
+    d = spec["d"]
+    fwd = d + 1                                   # d FFT passes + interpolation
+    adj = (1 if nchunks > 0 else 0) + 1 + d       # gridding chunks + tile reduction + d inverse passes
+    return fwd + adj
+
+
+def reduce_over_ranks(elapsed_s: float, units: float, world: int):
+    """Max elapsed time and summed units over ranks (identity for one rank)."""
+    if world <= 1:
+        return elapsed_s, units
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([elapsed_s], dtype=torch.float64, device=dev)
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, out_path: str | None = None):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.out_path = out_path
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu_index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        if self.out_path:
+            with open(self.out_path, "w") as f:
+                f.write("\n".join(self.lines) + "\n")
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ our arm
+
+STAGES = ("scale_pad_fft", "interp", "gridding", "ifft_crop_rescale")
+
+
+def run_workload(nf, torch, name: str, steps: int, warmup: int, dev, flush_bytes: int):
+    spec, om, x, _ = W.make_workload(name)
+    M = spec["M"]
+    plan = nf.NufftPlan(torch.from_numpy(om).to(dev), spec["Nd"], spec["Kd"], spec["Jd"])
+    info = plan.info()
+    xd = torch.from_numpy(x).to(dev)
+    grid = torch.empty(spec["Kd"], dtype=torch.complex64, device=dev)
+    y = torch.empty(M, dtype=torch.complex64, device=dev)
+    xo = torch.empty(spec["Nd"], dtype=torch.complex64, device=dev)
+    flush = torch.empty(flush_bytes // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        # the same kernel sequence as nufft_forward + nufft_adjoint, called stage by stage
+        plan.scale_pad_fft(xd, grid)
+        plan.interp(grid, y)
+        plan.gridding(y, grid)
+        plan.ifft_crop_rescale(grid, xo)
+
+    for _ in range(warmup):
+        step()
+        flush.fill_(1.0)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)] for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(float(k))                          # evict the previous step's data from L2
+        e = ev[k]
+        e[0].record(stream)
+        plan.scale_pad_fft(xd, grid)
+        e[1].record(stream)
+        plan.interp(grid, y)
+        e[2].record(stream)
+        plan.gridding(y, grid)
+        e[3].record(stream)
+        plan.ifft_crop_rescale(grid, xo)
+        e[4].record(stream)
+    torch.cuda.synchronize()
+    step_ms = [ev[k][0].elapsed_time(ev[k][-1]) for k in range(steps)]
+    stage_ms = {s: [ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(steps)] for i, s in enumerate(STAGES)}
+
+    # monolithic entry points, same work (checked to agree with the staged step)
+    for _ in range(2):
+        plan.forward(xd, y)
+        plan.adjoint(y, xo)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    mono = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0.record(stream)
+        plan.forward(xd, y)
+        plan.adjoint(y, xo)
+        e1.record(stream)
+        e1.synchronize()
+        mono.append(e0.elapsed_time(e1))
+
+    # end to end through the host-buffer entry points (pinned host memory)
+    x_h = torch.from_numpy(x).pin_memory()
+    y_h = torch.empty(M, dtype=torch.complex64).pin_memory()
+    xo_h = torch.empty(spec["Nd"], dtype=torch.complex64).pin_memory()
+    for _ in range(2):
+        plan.forward_host(x_h, y_h)
+        plan.adjoint_host(y_h, xo_h)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        plan.forward_host(x_h, y_h)
+        plan.adjoint_host(y_h, xo_h)
+    e2e_s = (time.perf_counter() - t0) / steps
+    nprod = int(np.prod(spec["Nd"]))
+    plan.close()
+    return dict(spec=spec, info=info, step_ms=step_ms, stage_ms=stage_ms, mono_ms=mono, e2e_s=e2e_s,
+                h2d=8 * (nprod + M), d2h=8 * (M + nprod))
+
+
+def roofline_for(res, peak_gbs: float, peak_kind: str, traffic: dict):
+    alg = algorithmic_bytes(res["spec"])
+    per_stage = {}
+    for s in STAGES:
+        ms = statistics.mean(res["stage_ms"][s])
+        gbs = alg[s] / (ms * 1e-3) / 1e9
+        per_stage[s] = {"ms": round(ms, 5), "alg_bytes": alg[s], "achieved_gbs": round(gbs, 1),
+                        "frac": round(gbs / peak_gbs, 4)}
+    dom = max(STAGES, key=lambda s: per_stage[s]["ms"])
+    r = per_stage[dom]
+    return dom, per_stage, {
+        "bound": "hbm", "kernel": dom, "achieved": r["achieved_gbs"], "peak": peak_gbs, "unit": "GB/s",
+        "frac": r["frac"], "peak_kind": f"{peak_kind} hbm_gbs", "traffic": traffic.get(dom),
+    }
+
+
+def ours(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    import paper_1710_03197_gb300 as nf
+
+    flush_bytes = 512 * 1024 * 1024
+    clocks_path = os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else None
+    if world > 1:
+        torch.distributed.barrier()
+    with ClockSampler(torch.cuda.current_device() if world == 1 else local, clocks_path) as clk:
+        res2 = run_workload(nf, torch, "radial2d_256", args.steps, args.warmup, dev, flush_bytes)
+        res3 = run_workload(nf, torch, "kooshball3d_128", args.steps, args.warmup, dev, flush_bytes)
+    torch.cuda.synchronize()
+
+    M2 = res2["spec"]["M"]
+    tot_ms = sum(res2["step_ms"])
+    elapsed, units = reduce_over_ranks(tot_ms * 1e-3, M2 * args.steps, world)
+    value = units / elapsed
+    e2e_el, e2e_units = reduce_over_ranks(res2["e2e_s"] * args.steps, M2 * args.steps, world)
+    M3 = res3["spec"]["M"]
+    el3, un3 = reduce_over_ranks(sum(res3["step_ms"]) * 1e-3, M3 * args.steps, world)
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    peak, peak_kind = load_peaks()
+    traffic = {}
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            traffic_all = json.load(f)
+        traffic = traffic_all.get("radial2d_256", {})
+        traffic3 = traffic_all.get("kooshball3d_128", {})
+    else:
+        traffic3 = {}
+    dom2, stages2, roof2 = roofline_for(res2, peak, peak_kind, traffic)
+    dom3, stages3, roof3 = roofline_for(res3, peak, peak_kind, traffic3)
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(seconds=args.cpu_seconds)
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(elapsed * 1e3 / args.steps, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "config": {"workload": "radial2d_256: 2D 256x256 image, 512x512 grid, J=6x6, golden-angle radial "
+                               "403 spokes x 512 samples (206,336 points), ellipse phantom",
+                   "step": "A x then A^H y (forward + adjoint)", "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": round(e2e_units / e2e_el, 1), "unit": UNIT, "h2d_bytes_per_step": res2["h2d"],
+                "d2h_bytes_per_step": res2["d2h"]},
+        "gpu_launches": launches_per_step(res2["spec"], res2["info"]["nchunks"]) * args.steps,
+        "roofline": roof2,
+        "stages": stages2,
+        "monolithic_ms_per_step": round(statistics.mean(res2["mono_ms"]), 5),
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+        "also": {"kooshball3d_128": {
+            "workload": "3D 128^3 image, 256^3 grid, J=6^3, kooshball 8192 Fibonacci spokes x 256 samples "
+                        "(2,097,152 points), complex normal image",
+            "value": round(un3 / el3, 1), "unit": UNIT, "ms_per_step": round(el3 * 1e3 / args.steps, 5),
+            "e2e": {"value": round(M3 / res3["e2e_s"], 1), "unit": UNIT, "h2d_bytes_per_step": res3["h2d"],
+                    "d2h_bytes_per_step": res3["d2h"]},
+            "gpu_launches": launches_per_step(res3["spec"], res3["info"]["nchunks"]) * args.steps,
+            "roofline": roof3, "stages": stages3,
+            "monolithic_ms_per_step": round(statistics.mean(res3["mono_ms"]), 5)}},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------------ oracle timing (CPU baseline / reference arm)
+
+def _oracle_setup(name="radial2d_256"):
+    import oracle
+    spec, om, x, noise = W.make_workload(name)
+    plan = oracle.make_plan(om, spec["Nd"], spec["Kd"], spec["Jd"])
+    return oracle, spec, plan, x
+
+
+def cpu_baseline(seconds: float = 10.0):
+    """The FP64 oracle's forward + adjoint on the full 2D workload, timed on the
+    host (plan precompute excluded), repeated until ``seconds`` have elapsed."""
+    oracle, spec, plan, x = _oracle_setup()
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        y = oracle.forward(plan, x)
+        oracle.adjoint(plan, y)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": round(spec["M"] * reps / el, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} forward+adjoint pairs on the full radial2d_256 workload (206,336 points), "
+                      f"FP64 numpy, plan excluded, {el:.1f} s"}
+
+
+def reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and rank != 0:
+        return
+    oracle, spec, plan, x = _oracle_setup()
+    for _ in range(args.warmup):
+        oracle.adjoint(plan, oracle.forward(plan, x))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.adjoint(plan, oracle.forward(plan, x))
+    el = time.perf_counter() - t0
+    value = spec["M"] * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el * 1e3 / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": "radial2d_256: 2D 256x256 image, 512x512 grid, J=6x6, golden-angle radial "
+                               "403 spokes x 512 samples (206,336 points), ellipse phantom",
+                   "step": "A x then A^H y (forward + adjoint)", "parallelism": "host CPU"},
+        "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} timed forward+adjoint pairs on the full workload, FP64 numpy, "
+                                   f"plan excluded"},
+        "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args(argv)
+    args.warmup = max(3, args.warmup)           # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        reference(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

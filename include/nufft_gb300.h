@@ -1,0 +1,193 @@
+/*
+ * nufft_gb300.h - C ABI of the GB300 (sm_103a) min-max NUFFT library.
+ *
+ * The library implements the NUFFT operator chain of PyNUFFT
+ * (J.-M. Lin, "Python Non-Uniform Fast Fourier Transform (PyNUFFT)",
+ * arXiv:1710.03197): the forward operator A = V F S (Section 2.1, Eq. 1),
+ * the adjoint A^H = S^H F^H V^H (Section 2.1.4, Eq. 2), the self-adjoint
+ * normal operator A^H A (Section 2.1.5), and the solvers of Section 2.2
+ * (conjugate gradient, L1TV-OLS Eqs. 11-20, L1TV-LAD Eqs. 21-31).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Complex data are interleaved float pairs (re, im), i.e. complex64.
+ *   An "image" is N_0 x ... x N_{d-1} complex values in C (row-major) order,
+ *   the order the paper uses for its interpolation matrix (Section 2.1.3).
+ *   "k-space data" y is M complex values in trajectory order.
+ *   The "grid" is K_0 x ... x K_{d-1} complex values in C order.
+ * - The trajectory om is M x d float32, row-major, in radians; column i pairs
+ *   with image axis i.  Sample m measures
+ *       y_m ~= sum_n x[n] exp(-i sum_i om[m,i] (n_i - N_i/2)).
+ * - Pointers named *_dev are CUDA device pointers; *_host are host pointers.
+ *   The caller owns every buffer it passes; no call keeps a caller pointer
+ *   after it returns.  The plan owns everything it allocates.
+ * - Calls on device buffers are asynchronous and ordered on the plan's
+ *   stream (set at plan creation, changeable with nufft_set_stream).  Input
+ *   buffers must stay valid and unmodified until the work completes.
+ * - Calls on host buffers (*_host) are synchronous.
+ * - Every call returns a status; on failure nufft_last_error() describes it.
+ * - A plan is not thread-safe: do not call into one plan from two host
+ *   threads at once.  Distinct plans are independent.
+ */
+#ifndef NUFFT_GB300_H
+#define NUFFT_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define NUFFT_OK        0
+#define NUFFT_EINVAL    1  /* bad argument (sizes, pointers, non-finite om, ...) */
+#define NUFFT_ENOMEM    2  /* a device or host allocation failed               */
+#define NUFFT_ECUDA     3  /* a CUDA runtime call or kernel launch failed       */
+#define NUFFT_ETIMEOUT  4  /* reserved: no call of this library waits on device */
+
+typedef struct nufft_plan nufft_plan_t;
+
+/*
+ * nufft_plan - precompute the min-max interpolator for one trajectory.
+ *
+ * Section 2.1 (Eq. 1) and Section 2.1.3: the interpolation V uses the min-max
+ * interpolator of Fessler and Sutton (the paper's default kernel), whose
+ * scaling S is chosen together with it to keep the off-grid error small.  The
+ * plan computes, in FP64 on the GPU: the per-dimension scaling factors s_i
+ * (reciprocal Kaiser-Bessel transform, alpha = 2.34 J), the J x J min-max
+ * matrix inverse per dimension, and per point and dimension the first
+ * neighbour and the J interpolation coefficients (stored as complex64).
+ * Points are then sorted by grid tile (counting sort by tile, stable in m),
+ * which replaces the paper's CSR matrix and pre-indexes (Section 2.1.2,
+ * Section 2.2.3) with per-point records read by the kernels.
+ *
+ *   d       number of dimensions, 1..3
+ *   Nd      image size per dimension (d ints): even, 2 <= N_i <= K_i
+ *   Kd      oversampled grid per dimension (d ints): a power of two, 16..1024
+ *   Jd      neighbours per dimension (d ints): 1 <= J_i <= 16
+ *   M       number of k-space points, 0 <= M < 2^31
+ *   om_dev  M x d float32 device array (may be NULL when M == 0); every value
+ *           finite with |om| <= 2^20.  Read during the call only.
+ *   stream  cudaStream_t to order all work of this plan on (NULL = legacy
+ *           default stream).  The plan creation itself synchronizes it.
+ *   out     receives the new plan; set to NULL on failure.
+ *
+ * Errors: NUFFT_EINVAL (sizes out of range, om non-finite or too large),
+ * NUFFT_ENOMEM, NUFFT_ECUDA.  nufft_last_error(NULL) describes a failure.
+ */
+int nufft_plan(int d, const int* Nd, const int* Kd, const int* Jd, int64_t M,
+               const float* om_dev, void* stream, nufft_plan_t** out);
+
+/* Release every device and host buffer the plan owns.  NULL is a no-op.
+ * Synchronizes the plan's stream first. */
+int nufft_plan_destroy(nufft_plan_t* plan);
+
+/* Message for the last failure on this plan (plan == NULL: last failure of a
+ * plan-less call on this host thread).  Never NULL; valid until the next call. */
+const char* nufft_last_error(const nufft_plan_t* plan);
+
+/* Change the stream the plan's work is ordered on (cudaStream_t as void*). */
+int nufft_set_stream(nufft_plan_t* plan, void* stream);
+
+/*
+ * Plan description.  info receives 16 int64 values:
+ *   [0] d, [1] M, [2..4] N_i, [5..7] K_i, [8..10] J_i,
+ *   [11] number of tiles (bins), [12] number of gridding chunks,
+ *   [13] device bytes owned by the plan, [14..15] tile edge for dims 0 and d-1.
+ */
+int nufft_plan_info(const nufft_plan_t* plan, int64_t* info);
+
+/*
+ * Copy the plan's per-point interpolator back to the host, in trajectory
+ * order (Section 2.1.3; the min-max coefficients of Fessler and Sutton):
+ *   kfirst_host  M x d int32: grid index of the first neighbour,
+ *                (floor-based offset + 1) mod K_i; neighbours are
+ *                kfirst + j mod K_i, j = 0..J_i-1.
+ *   coef_host    for i = 0..d-1 in turn, M x J_i complex64 coefficients
+ *                (float pairs), i.e. sum_i M*J_i*2 floats in total.
+ *   s_host       for i = 0..d-1 in turn, the N_i scaling factors (float).
+ *   perm_host    M int32: perm[r] = trajectory index of the r-th point in
+ *                tile-sorted order (may be NULL to skip).
+ * Any output pointer may be NULL to skip it.  Synchronous.
+ */
+int nufft_plan_get_interpolator(const nufft_plan_t* plan, int32_t* kfirst_host,
+                                float* coef_host, float* s_host, int32_t* perm_host);
+
+/* y = A x = V F S x (Section 2.1, Eq. 1).  x_dev: image, y_dev: M values.
+ * x is not modified.  No allocation. */
+int nufft_forward(nufft_plan_t* plan, const float* x_dev, float* y_dev);
+
+/* x = A^H y = S^H F^H V^H y (Section 2.1.4, Eq. 2): the exact conjugate
+ * transpose of nufft_forward (no 1/K normalisation).  No allocation. */
+int nufft_adjoint(nufft_plan_t* plan, const float* y_dev, float* x_dev);
+
+/* out = A^H A x (Section 2.1.5, the normal operator of Eq. 4), computed as
+ * S^H F^H (V^H V) F S x with V^H V applied per grid tile.  x and out may not
+ * alias.  No allocation. */
+int nufft_selfadjoint(nufft_plan_t* plan, const float* x_dev, float* out_dev);
+
+/* Host-buffer forms of nufft_forward / nufft_adjoint: copy the input to the
+ * plan's device staging buffer, run the operator, copy the result back and
+ * synchronize.  Page-locked host memory gives the fastest copies. */
+int nufft_forward_host(nufft_plan_t* plan, const float* x_host, float* y_host);
+int nufft_adjoint_host(nufft_plan_t* plan, const float* y_host, float* x_host);
+
+/*
+ * Stage calls (the pieces nufft_forward / nufft_adjoint are made of):
+ *   nufft_scale_pad_fft      grid = F pad(S x)  (Sections 2.1.1-2.1.2)
+ *   nufft_interp             y = V grid         (Section 2.1.3)
+ *   nufft_gridding           grid = V^H y       (Section 2.1.3, "gridding")
+ *   nufft_ifft_crop_rescale  x = S^H crop(F^H grid) (Section 2.1.2, Table 1
+ *                            "IFFT" and "Rescaling"); grid_dev is used as
+ *                            work space and left undefined.
+ * grid_dev is K_0 x ... x K_{d-1} complex64.  The transforms are pruned
+ * (zero lines of the padded image are never read, lines outside the crop are
+ * never written back) but nufft_scale_pad_fft leaves every grid cell holding
+ * F pad(S x), and nufft_gridding writes every grid cell.
+ */
+int nufft_scale_pad_fft(nufft_plan_t* plan, const float* x_dev, float* grid_dev);
+int nufft_interp(nufft_plan_t* plan, const float* grid_dev, float* y_dev);
+int nufft_gridding(nufft_plan_t* plan, const float* y_dev, float* grid_dev);
+int nufft_ifft_crop_rescale(nufft_plan_t* plan, float* grid_dev, float* x_dev);
+
+/*
+ * solve_cg - conjugate gradient on the normal equation A^H A x = A^H y
+ * (Section 2.1.5 Eq. 4; Section 2.2.2 Eqs. 7-9 give the paper's k-space form,
+ * this is the image-domain form).  Exactly maxiter iterations, no early exit;
+ * inner products accumulated in FP64 with a fixed reduction order.
+ *   y_dev  M k-space values; x_dev in: initial image x0, out: the result.
+ * Allocates the solver work space on first use (kept by the plan).
+ */
+int solve_cg(nufft_plan_t* plan, const float* y_dev, float* x_dev, int maxiter);
+
+/*
+ * solve_l1tv_ols - L1 total-variation regularised least squares by variable
+ * splitting (Section 2.2.3, Eqs. 11-20):
+ *   K = mu A^H A + lambda sum_i grad_i^T grad_i;
+ *   per inner iteration: rhs = mu A^H y^k + lambda sum_i grad_i^T (d_i - b_i),
+ *   x = K^{-1} rhs (cg_iters CG steps warm-started from x),
+ *   d_i = shrink(grad_i x + b_i, 1/lambda), b_i += grad_i x - d_i;
+ *   per outer iteration: A^H y^{k+1} = A^H y^k + A^H y - A^H A x.
+ * grad_i is the periodic forward difference along image axis i (every axis).
+ *   maxiter  outer iterations (>= 0), inner: split iterations per outer (>= 1),
+ *   cg_iters CG steps per K-solve (>= 1), mu > 0, lambda > 0.
+ *   x_dev in: initial image, out: result.  d_i = b_i = 0 at the start.
+ */
+int solve_l1tv_ols(nufft_plan_t* plan, const float* y_dev, float* x_dev, int maxiter,
+                   int inner, int cg_iters, double mu, double lambda);
+
+/*
+ * solve_l1tv_lad - L1 total-variation regularised least absolute deviation
+ * (Section 2.2.3, Eqs. 21-31): as solve_l1tv_ols with the data term split
+ * too: rhs adds mu (d_f - b_f); after the shrink steps,
+ *   d_f = shrink(A^H A x - A^H y + b_f, 1/mu), b_f += A^H A x - A^H y - d_f
+ * (the printed "+ b_y" of Eq. 26 is read as b_f).
+ */
+int solve_l1tv_lad(nufft_plan_t* plan, const float* y_dev, float* x_dev, int maxiter,
+                   int inner, int cg_iters, double mu, double lambda);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NUFFT_GB300_H */

@@ -1,0 +1,122 @@
+// capi.cu - operator entry points of the C ABI: A (Eq. 1), A^H (Eq. 2),
+// A^H A (Section 2.1.5), their host-buffer forms and the stage calls.
+#include "internal.cuh"
+
+using namespace nufft;
+
+namespace {
+
+int check_plan(nufft_plan_t* p) {
+  if (!p) return set_error(nullptr, NUFFT_EINVAL, "plan is NULL");
+  return NUFFT_OK;
+}
+
+int check_ptr(nufft_plan_t* p, const void* ptr, int64_t count, const char* name) {
+  if (count > 0 && !ptr) return set_error(p, NUFFT_EINVAL, "%s is NULL", name);
+  return NUFFT_OK;
+}
+
+#define TRY(x)                 \
+  do {                         \
+    int _rc = (x);             \
+    if (_rc != NUFFT_OK) return _rc; \
+  } while (0)
+
+int forward_impl(nufft_plan_t* p, const float2* x, float2* y) {
+  if (p->M == 0) return NUFFT_OK;
+  TRY(launch_fft_forward(p, x, p->grid));
+  return launch_interp(p, p->grid, y);
+}
+
+int adjoint_impl(nufft_plan_t* p, const float2* y, float2* x) {
+  TRY(launch_gridding(p, y, p->grid));
+  return launch_fft_inverse(p, p->grid, x);
+}
+
+}  // namespace
+
+namespace nufft {
+// A^H A x, used by the solvers too.
+int selfadjoint_impl(nufft_plan_t* p, const float2* x, float2* out) {
+  TRY(launch_fft_forward(p, x, p->grid));
+  TRY(launch_interp(p, p->grid, p->ytmp));
+  TRY(launch_gridding(p, p->ytmp, p->grid));
+  return launch_fft_inverse(p, p->grid, out);
+}
+int forward_dev(nufft_plan_t* p, const float2* x, float2* y) { return forward_impl(p, x, y); }
+int adjoint_dev(nufft_plan_t* p, const float2* y, float2* x) { return adjoint_impl(p, y, x); }
+}  // namespace nufft
+
+extern "C" int nufft_forward(nufft_plan_t* p, const float* x_dev, float* y_dev) {
+  TRY(check_plan(p));
+  TRY(check_ptr(p, x_dev, p->Nprod, "x_dev"));
+  TRY(check_ptr(p, y_dev, p->M, "y_dev"));
+  return forward_impl(p, reinterpret_cast<const float2*>(x_dev), reinterpret_cast<float2*>(y_dev));
+}
+
+extern "C" int nufft_adjoint(nufft_plan_t* p, const float* y_dev, float* x_dev) {
+  TRY(check_plan(p));
+  TRY(check_ptr(p, y_dev, p->M, "y_dev"));
+  TRY(check_ptr(p, x_dev, p->Nprod, "x_dev"));
+  return adjoint_impl(p, reinterpret_cast<const float2*>(y_dev), reinterpret_cast<float2*>(x_dev));
+}
+
+extern "C" int nufft_selfadjoint(nufft_plan_t* p, const float* x_dev, float* out_dev) {
+  TRY(check_plan(p));
+  TRY(check_ptr(p, x_dev, p->Nprod, "x_dev"));
+  TRY(check_ptr(p, out_dev, p->Nprod, "out_dev"));
+  if ((const void*)x_dev == (const void*)out_dev) return set_error(p, NUFFT_EINVAL, "x_dev and out_dev alias");
+  return selfadjoint_impl(p, reinterpret_cast<const float2*>(x_dev), reinterpret_cast<float2*>(out_dev));
+}
+
+extern "C" int nufft_forward_host(nufft_plan_t* p, const float* x_host, float* y_host) {
+  TRY(check_plan(p));
+  TRY(check_ptr(p, x_host, p->Nprod, "x_host"));
+  TRY(check_ptr(p, y_host, p->M, "y_host"));
+  NUFFT_CUDA_TRY(p, cudaMemcpyAsync(p->x_stage, x_host, p->Nprod * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
+  TRY(forward_impl(p, p->x_stage, p->y_stage));
+  if (p->M > 0)
+    NUFFT_CUDA_TRY(p, cudaMemcpyAsync(y_host, p->y_stage, p->M * sizeof(float2), cudaMemcpyDeviceToHost, p->stream));
+  NUFFT_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+  return NUFFT_OK;
+}
+
+extern "C" int nufft_adjoint_host(nufft_plan_t* p, const float* y_host, float* x_host) {
+  TRY(check_plan(p));
+  TRY(check_ptr(p, y_host, p->M, "y_host"));
+  TRY(check_ptr(p, x_host, p->Nprod, "x_host"));
+  if (p->M > 0)
+    NUFFT_CUDA_TRY(p, cudaMemcpyAsync(p->y_stage, y_host, p->M * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
+  TRY(adjoint_impl(p, p->y_stage, p->x_stage));
+  NUFFT_CUDA_TRY(p, cudaMemcpyAsync(x_host, p->x_stage, p->Nprod * sizeof(float2), cudaMemcpyDeviceToHost, p->stream));
+  NUFFT_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+  return NUFFT_OK;
+}
+
+extern "C" int nufft_scale_pad_fft(nufft_plan_t* p, const float* x_dev, float* grid_dev) {
+  TRY(check_plan(p));
+  TRY(check_ptr(p, x_dev, p->Nprod, "x_dev"));
+  TRY(check_ptr(p, grid_dev, p->Kprod, "grid_dev"));
+  return launch_fft_forward(p, reinterpret_cast<const float2*>(x_dev), reinterpret_cast<float2*>(grid_dev));
+}
+
+extern "C" int nufft_interp(nufft_plan_t* p, const float* grid_dev, float* y_dev) {
+  TRY(check_plan(p));
+  TRY(check_ptr(p, grid_dev, p->Kprod, "grid_dev"));
+  TRY(check_ptr(p, y_dev, p->M, "y_dev"));
+  return launch_interp(p, reinterpret_cast<const float2*>(grid_dev), reinterpret_cast<float2*>(y_dev));
+}
+
+extern "C" int nufft_gridding(nufft_plan_t* p, const float* y_dev, float* grid_dev) {
+  TRY(check_plan(p));
+  TRY(check_ptr(p, y_dev, p->M, "y_dev"));
+  TRY(check_ptr(p, grid_dev, p->Kprod, "grid_dev"));
+  return launch_gridding(p, reinterpret_cast<const float2*>(y_dev), reinterpret_cast<float2*>(grid_dev));
+}
+
+extern "C" int nufft_ifft_crop_rescale(nufft_plan_t* p, float* grid_dev, float* x_dev) {
+  TRY(check_plan(p));
+  TRY(check_ptr(p, grid_dev, p->Kprod, "grid_dev"));
+  TRY(check_ptr(p, x_dev, p->Nprod, "x_dev"));
+  return launch_fft_inverse(p, reinterpret_cast<float2*>(grid_dev), reinterpret_cast<float2*>(x_dev));
+}

@@ -1,0 +1,325 @@
+// fft.cu - scaling + zero-padding + oversampled FFT, and inverse FFT + crop +
+// rescaling, as pruned line passes over the K^d grid.
+//
+// Section 2.1.1 (scaling S), Section 2.1.2 (zero-padding and oversampled FFT
+// F; the inverse FFT followed by the array copy back), Table 1 rows S, F, F^H,
+// S^H.  The paper runs S, a pre-indexed copy and a library FFT as separate
+// steps over the whole K^d array.  Here the d-dimensional transform is done
+// one axis at a time, and each pass is pruned:
+//   forward, axis a: lines whose coordinates on axes < a lie in the padded
+//     image's footprint (N_i of the K_i positions), all K on axes > a; only
+//     the N_a non-zero inputs of a line are read; all K_a outputs written.
+//     The first pass (last axis) reads the image itself and applies S, so
+//     the padded array is never materialised.
+//   inverse, axis a: lines over the crop footprint on axes < a, all K on
+//     axes > a; all K_a inputs read, only the N_a cropped outputs written;
+//     the last pass (last axis) applies S^H and writes the image.
+// Padded position of image index n along an axis: g = (n - N/2) mod K.
+//
+// Each line is transformed in shared memory by a Stockham auto-sort FFT
+// (mixed radix: one radix-2 or radix-4 stage, then radix-8 stages), each
+// thread holding 8 values per stage.  Twiddles exp(-2 pi i k / K) come from a
+// table computed in FP64 at plan time.
+#include "internal.cuh"
+
+namespace nufft {
+namespace {
+
+struct FftArgs {
+  const float2* src;
+  float2* dst;
+  const float2* tw;           // K_a forward twiddles
+  const float* s_axis;        // scaling of axis a (image side only)
+  const float* s_lead[kMaxDim];
+  int a;
+  int Na;                     // N_a
+  int lead_N[kMaxDim];
+  int lead_K[kMaxDim];
+  int64_t lead_stride[kMaxDim];
+  int64_t nouter;             // prod_{i<a} N_i
+  int64_t inner;              // prod_{i>a} K_i (grid stride of axis a)
+  int src_image;              // forward first pass: read the image, apply S
+  int dst_image;              // inverse last pass: write the image, apply S^H
+};
+
+template <bool INV>
+__device__ __forceinline__ float2 rot90(float2 z) {  // z * (-i) forward, z * (+i) inverse
+  return INV ? make_float2(-z.y, z.x) : make_float2(z.y, -z.x);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft2(float2* v) {
+  float2 a = v[0];
+  v[0] = cadd(a, v[1]);
+  v[1] = csub(a, v[1]);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& v0, float2& v1, float2& v2, float2& v3) {
+  float2 a = cadd(v0, v2), b = csub(v0, v2), c = cadd(v1, v3), e = rot90<INV>(csub(v1, v3));
+  v0 = cadd(a, c);
+  v1 = cadd(b, e);
+  v2 = csub(a, c);
+  v3 = csub(b, e);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft8(float2* v) {
+  const float h = 0.70710678118654752440f;
+  float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<INV>(e0, e1, e2, e3);
+  dft4<INV>(o0, o1, o2, o3);
+  // o_k *= W8^k, W8 = exp(-+ 2 pi i / 8)
+  o1 = INV ? make_float2(h * (o1.x - o1.y), h * (o1.x + o1.y))
+           : make_float2(h * (o1.x + o1.y), h * (o1.y - o1.x));
+  o2 = rot90<INV>(o2);
+  o3 = INV ? make_float2(h * (-o3.x - o3.y), h * (o3.x - o3.y))
+           : make_float2(h * (o3.y - o3.x), h * (-o3.x - o3.y));
+  v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+  v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
+  v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
+  v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2* v) {
+  if (R == 2) dft2<INV>(v);
+  else if (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
+  else dft8<INV>(v);
+}
+
+constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
+
+// Shared-memory position of element p of the line owned by lane-group b.
+template <int L, bool STRIDED>
+struct SmemIdx {
+  static constexpr int kB = STRIDED ? 8 : ((L / 8) >= 256 ? 1 : 256 / (L / 8));
+  static constexpr int kLinePitch = L + L / 8;          // contiguous layout, one pad per 8
+  static constexpr int kWords = STRIDED ? L * (kB + 1) : kB * kLinePitch;
+  __device__ __forceinline__ static int at(int b, int p) {
+    return STRIDED ? p * (kB + 1) + b : b * kLinePitch + p + (p >> 3);
+  }
+};
+
+// One Stockham stage of radix R over span Ns, in place in shared memory.
+template <int L, bool STRIDED, bool INV, int R>
+__device__ __forceinline__ void stage(float2* sm, int b, int t, int Ns, const float2* __restrict__ tw) {
+  constexpr int TPL = L / 8;
+  constexpr int Q = 8 / R;
+  float2 v[Q][R];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int j = t + q * TPL;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[q][r] = sm[SmemIdx<L, STRIDED>::at(b, j + r * (L / R))];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int j = t + q * TPL;
+    const int k = j & (Ns - 1);
+    if (Ns > 1) {
+      const int step = L / (Ns * R);
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        float2 w = __ldg(&tw[r * k * step]);
+        if (INV) w.y = -w.y;
+        v[q][r] = cmul(v[q][r], w);
+      }
+    }
+    dft<R, INV>(v[q]);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) sm[SmemIdx<L, STRIDED>::at(b, base + r * Ns)] = v[q][r];
+  }
+  __syncthreads();
+}
+
+template <int L, bool STRIDED, bool INV>
+__global__ void __launch_bounds__(STRIDED ? L : 256)
+k_fft_pass(const FftArgs A) {
+  using SI = SmemIdx<L, STRIDED>;
+  constexpr int TPL = L / 8;
+  constexpr int B = SI::kB;
+  extern __shared__ float2 sm[];
+
+  const int tid = threadIdx.x;
+  int b, t;
+  int64_t o, in;
+  if (STRIDED) {
+    b = tid & 7;
+    t = tid >> 3;
+    const int64_t nib = A.inner >> 3;
+    o = blockIdx.x / nib;
+    in = (blockIdx.x % nib) * 8 + b;
+  } else {
+    b = tid / TPL;
+    t = tid % TPL;
+    o = (int64_t)blockIdx.x * B + b;
+    in = 0;
+  }
+  const bool live = o < A.nouter;
+
+  // Outer coordinates: image index on axes < a, mapped to padded grid positions.
+  int64_t goff = 0;
+  float slead = 1.0f;
+  if (live) {
+    int64_t rem = o;
+    for (int i = A.a - 1; i >= 0; --i) {
+      const int n = (int)(rem % A.lead_N[i]);
+      rem /= A.lead_N[i];
+      const int gi = (n - A.lead_N[i] / 2 + A.lead_K[i]) & (A.lead_K[i] - 1);
+      goff += (int64_t)gi * A.lead_stride[i];
+      if (A.src_image || A.dst_image) slead *= A.s_lead[i][n];
+    }
+  }
+  const int half = A.Na >> 1;
+  const int64_t stride = A.inner;
+
+  // ---- load the line (pruned on the forward side)
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int p = t + k * TPL;
+    float2 v = make_float2(0.f, 0.f);
+    if (live) {
+      if (!INV) {
+        const bool in_image = (p < half) || (p >= L - half);
+        if (in_image) {
+          if (A.src_image) {
+            const int n = p < half ? p + half : p - L + half;
+            v = cscale(__ldg(&A.src[o * A.Na + n]), A.s_axis[n] * slead);
+          } else {
+            v = A.src[goff + (int64_t)p * stride + in];
+          }
+        }
+      } else {
+        v = A.src[goff + (int64_t)p * stride + in];
+      }
+    }
+    sm[SI::at(b, p)] = v;
+  }
+  __syncthreads();
+
+  // ---- transform
+  constexpr int LOG = ilog2(L);
+  constexpr int R0 = 1 << (LOG % 3);
+  int Ns = 1;
+  if (R0 == 2) { stage<L, STRIDED, INV, 2>(sm, b, t, Ns, A.tw); Ns *= 2; }
+  if (R0 == 4) { stage<L, STRIDED, INV, 4>(sm, b, t, Ns, A.tw); Ns *= 4; }
+#pragma unroll
+  for (int s = 0; s < LOG / 3; ++s) { stage<L, STRIDED, INV, 8>(sm, b, t, Ns, A.tw); Ns *= 8; }
+
+  // ---- store (pruned on the inverse side)
+  if (!live) return;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int p = t + k * TPL;
+    const float2 v = sm[SI::at(b, p)];
+    if (!INV) {
+      A.dst[goff + (int64_t)p * stride + in] = v;
+    } else {
+      const bool in_image = (p < half) || (p >= L - half);
+      if (!in_image) continue;
+      if (A.dst_image) {
+        const int n = p < half ? p + half : p - L + half;
+        A.dst[o * A.Na + n] = cscale(v, A.s_axis[n] * slead);
+      } else {
+        A.dst[goff + (int64_t)p * stride + in] = v;
+      }
+    }
+  }
+}
+
+template <int L, bool STRIDED, bool INV>
+cudaError_t launch_L(const FftArgs& A, cudaStream_t st) {
+  using SI = SmemIdx<L, STRIDED>;
+  const size_t smem = (size_t)SI::kWords * sizeof(float2);
+  static bool attr_set = false;  // per process; the attribute is per function
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_fft_pass<L, STRIDED, INV>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  int64_t blocks;
+  int threads;
+  if (STRIDED) {
+    blocks = A.nouter * (A.inner / 8);
+    threads = L;  // 8 lines x L/8 threads
+  } else {
+    blocks = (A.nouter + SI::kB - 1) / SI::kB;
+    threads = SI::kB * (L / 8);
+  }
+  if (blocks == 0) return cudaSuccess;
+  k_fft_pass<L, STRIDED, INV><<<(unsigned)blocks, threads, smem, st>>>(A);
+  return cudaGetLastError();
+}
+
+template <bool STRIDED, bool INV>
+cudaError_t launch_any(int L, const FftArgs& A, cudaStream_t st) {
+  switch (L) {
+    case 16: return launch_L<16, STRIDED, INV>(A, st);
+    case 32: return launch_L<32, STRIDED, INV>(A, st);
+    case 64: return launch_L<64, STRIDED, INV>(A, st);
+    case 128: return launch_L<128, STRIDED, INV>(A, st);
+    case 256: return launch_L<256, STRIDED, INV>(A, st);
+    case 512: return launch_L<512, STRIDED, INV>(A, st);
+    case 1024: return launch_L<1024, STRIDED, INV>(A, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+FftArgs make_args(const nufft_plan_t* p, int a) {
+  FftArgs A;
+  memset(&A, 0, sizeof(A));
+  const Geom& g = p->g;
+  A.a = a;
+  A.Na = g.N[a];
+  A.tw = p->twiddle + p->tw_off[a];
+  A.s_axis = p->s + p->s_off[a];
+  A.nouter = 1;
+  for (int i = 0; i < a; ++i) {
+    A.lead_N[i] = g.N[i];
+    A.lead_K[i] = g.K[i];
+    A.lead_stride[i] = g.Kstride[i];
+    A.s_lead[i] = p->s + p->s_off[i];
+    A.nouter *= g.N[i];
+  }
+  A.inner = g.Kstride[a];
+  return A;
+}
+
+}  // namespace
+
+int launch_fft_forward(nufft_plan_t* p, const float2* x, float2* grid) {
+  const int d = p->g.d;
+  for (int a = d - 1; a >= 0; --a) {
+    FftArgs A = make_args(p, a);
+    A.src_image = (a == d - 1);
+    A.src = A.src_image ? x : grid;
+    A.dst = grid;
+    const bool strided = A.inner > 1;
+    cudaError_t e = strided ? launch_any<true, false>(p->g.K[a], A, p->stream)
+                            : launch_any<false, false>(p->g.K[a], A, p->stream);
+    if (e != cudaSuccess) return cuda_check(p, e, "forward FFT pass");
+  }
+  return NUFFT_OK;
+}
+
+int launch_fft_inverse(nufft_plan_t* p, float2* grid, float2* x) {
+  const int d = p->g.d;
+  for (int a = 0; a < d; ++a) {
+    FftArgs A = make_args(p, a);
+    A.dst_image = (a == d - 1);
+    A.src = grid;
+    A.dst = A.dst_image ? x : grid;
+    const bool strided = A.inner > 1;
+    cudaError_t e = strided ? launch_any<true, true>(p->g.K[a], A, p->stream)
+                            : launch_any<false, true>(p->g.K[a], A, p->stream);
+    if (e != cudaSuccess) return cuda_check(p, e, "inverse FFT pass");
+  }
+  return NUFFT_OK;
+}
+
+}  // namespace nufft

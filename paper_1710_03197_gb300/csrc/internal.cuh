@@ -1,0 +1,129 @@
+// internal.cuh - plan layout and kernel launchers shared by the library's
+// translation units.  Not part of the public ABI (see include/nufft_gb300.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "../../include/nufft_gb300.h"
+
+namespace nufft {
+
+constexpr int kMaxDim = 3;
+constexpr int kMaxJ = 16;
+constexpr int kMinK = 16;
+constexpr int kMaxK = 1024;
+// Points per gridding chunk: a tile's points are cut into chunks of at most
+// this many so that a dense tile (the centre of a radial trajectory) is spread
+// over several CTAs.
+constexpr int kChunkPoints = 2048;
+
+// Geometry of the oversampled grid and of the tile decomposition.
+struct Geom {
+  int d;
+  int N[kMaxDim];      // image size
+  int K[kMaxDim];      // grid size (power of two)
+  int J[kMaxDim];      // neighbours
+  int T[kMaxDim];      // tile edge
+  int nb[kMaxDim];     // tiles per dimension = K / T
+  int P[kMaxDim];      // padded tile edge = T + J - 1
+  int64_t Kstride[kMaxDim];  // C-order strides of the grid
+  int64_t nbins;
+  int64_t padded_cells;      // prod P
+};
+
+// Per-point interpolator in tile-sorted order ("structure of arrays").
+struct Points {
+  int64_t M;
+  const int32_t* kf;     // [d][M]  first neighbour, wrapped into [0, K)
+  const float2* coef;    // dim i starts at coef + coef_off[i]; layout [J_i][M]
+  int64_t coef_off[kMaxDim];
+  const int32_t* perm;   // sorted position -> trajectory index
+};
+
+struct Chunk {
+  int32_t bin;
+  int32_t start;   // first sorted point
+  int32_t count;   // points in this chunk
+  int32_t pad;
+};
+
+}  // namespace nufft
+
+struct nufft_plan {
+  nufft::Geom g;
+  int64_t M;
+  int64_t Nprod;
+  int64_t Kprod;
+  cudaStream_t stream;
+
+  // plan-owned device memory
+  float* s;                 // scaling, dim i at s + s_off[i]
+  int64_t s_off[nufft::kMaxDim];
+  float2* twiddle;          // forward twiddles exp(-2 pi i k / K_i), dim i at tw_off[i]
+  int64_t tw_off[nufft::kMaxDim];
+  int32_t* kf;              // [d][M] sorted
+  float2* coef;             // [sum_i J_i][M] sorted
+  int64_t coef_off[nufft::kMaxDim];
+  int32_t* perm;            // [M]
+  int32_t* bin_start;       // [nbins + 1]
+  nufft::Chunk* chunks;     // [nchunks]
+  int32_t* bin_chunk;       // [nbins + 1] chunk range of each bin
+  int64_t nchunks;
+  float2* tiles;            // [nchunks][padded_cells] gridding partial tiles
+  float2* grid;             // [Kprod] oversampled grid work space
+  float2* ytmp;             // [M] work space of the self-adjoint operator
+  float2* x_stage;          // [Nprod] staging for host-buffer calls
+  float2* y_stage;          // [M]
+  int64_t device_bytes;
+
+  // solver work space (allocated on first solver call)
+  void* solver_ws;
+  int64_t solver_ws_bytes;
+
+  char err[512];
+};
+
+namespace nufft {
+
+// ------------------------------------------------------------------ errors
+int set_error(nufft_plan_t* p, int code, const char* fmt, ...);
+int cuda_check(nufft_plan_t* p, cudaError_t e, const char* what);
+#define NUFFT_CUDA_TRY(p, call)                                   \
+  do {                                                            \
+    cudaError_t _e = (call);                                      \
+    if (_e != cudaSuccess) return ::nufft::cuda_check((p), _e, #call); \
+  } while (0)
+
+// ------------------------------------------------------------------ launchers
+// FFT passes (fft.cu).  Forward: grid = F pad(S x).  Inverse: x = S crop(F^H grid).
+int launch_fft_forward(nufft_plan_t* p, const float2* x, float2* grid);
+int launch_fft_inverse(nufft_plan_t* p, float2* grid, float2* x);
+
+// Interpolation and gridding (interp.cu).
+int launch_interp(nufft_plan_t* p, const float2* grid, float2* y);
+int launch_gridding(nufft_plan_t* p, const float2* y, float2* grid);
+
+// Plan-time helpers (plan.cu).
+Points points_view(const nufft_plan_t* p);
+
+}  // namespace nufft
+
+// ------------------------------------------------------------------ complex helpers
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // conj(a) * b
+  return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+  return make_float2(a.x + b.x, a.y + b.y);
+}
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  return make_float2(a.x - b.x, a.y - b.y);
+}
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) {
+  return make_float2(a.x * s, a.y * s);
+}

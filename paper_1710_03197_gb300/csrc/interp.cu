@@ -1,0 +1,298 @@
+// interp.cu - interpolation V (grid -> k-space) and gridding V^H
+// (k-space -> grid) with the min-max interpolator.
+//
+// Section 2.1.3: V maps the oversampled grid to the M non-uniform points, each
+// point combining its J^d neighbours; gridding is its conjugate transpose.
+// The paper stores V as a CSR matrix and runs a sparse matrix-vector product
+// for both directions.  Here each point keeps only its first neighbour per
+// dimension and J coefficients per dimension (the d-dimensional weight is their
+// product), and points are sorted by grid tile at plan time.
+//
+// Interpolation: a group of J_last lanes handles one point; lane l owns the
+// l-th neighbour along the last (contiguous) axis, so the group reads J_last
+// consecutive grid cells per neighbour row, and the partial sums are combined
+// with warp shuffles.
+//
+// Gridding: one CTA per chunk of a tile's points accumulates conj(weight) * y
+// into a shared-memory copy of the tile extended by J-1 cells per dimension
+// (the "padded tile"), then writes the padded tile to a per-chunk buffer.  A
+// second kernel forms every grid cell of a tile as the sum, in a fixed order,
+// of the padded tiles that cover it (its own tile's chunks and those of the
+// 2^d - 1 lower neighbour tiles).  No global atomics; every grid cell is
+// written exactly once.
+#include "internal.cuh"
+
+namespace nufft {
+namespace {
+
+// ---------------------------------------------------------------- interpolation
+template <int D, int JF>
+__global__ void __launch_bounds__(256)
+k_interp(const float2* __restrict__ grid, float2* __restrict__ y, const Points P, const Geom g) {
+  const int G = JF > 0 ? JF : g.J[D - 1];
+  const int lane = threadIdx.x & 31;
+  const int per_warp = 32 / G;
+  const int sub = lane / G;
+  const int l = lane - sub * G;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t i = warp * per_warp + sub;
+  const bool active = (sub < per_warp) && (i < P.M);
+
+  float2 part = make_float2(0.f, 0.f);
+  if (active) {
+    const int J0 = JF > 0 ? JF : g.J[0];
+    const int J1 = JF > 0 ? JF : (D > 1 ? g.J[1] : 1);
+    const int kl = P.kf[(int64_t)(D - 1) * P.M + i];
+    const int Klast = g.K[D - 1];
+    const int gl = (kl + l) & (Klast - 1);
+    const float2 cl = P.coef[P.coef_off[D - 1] + (int64_t)l * P.M + i];
+    if (D == 1) {
+      part = cmul(cl, __ldg(&grid[gl]));
+    } else if (D == 2) {
+      const int k0 = P.kf[i];
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j0 = 0; j0 < (JF > 0 ? JF : kMaxJ); ++j0) {
+        if (JF == 0 && j0 >= J0) break;
+        const float2 c0 = P.coef[P.coef_off[0] + (int64_t)j0 * P.M + i];
+        const int64_t row = (int64_t)((k0 + j0) & (g.K[0] - 1)) * g.Kstride[0];
+        acc = cadd(acc, cmul(c0, __ldg(&grid[row + gl])));
+      }
+      part = cmul(cl, acc);
+    } else {
+      const int k0 = P.kf[i];
+      const int k1 = P.kf[P.M + i];
+      float2 c1v[JF > 0 ? JF : kMaxJ];
+#pragma unroll
+      for (int j1 = 0; j1 < (JF > 0 ? JF : kMaxJ); ++j1) {
+        if (JF == 0 && j1 >= J1) break;
+        c1v[j1] = P.coef[P.coef_off[1] + (int64_t)j1 * P.M + i];
+      }
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 1
+      for (int j0 = 0; j0 < J0; ++j0) {
+        const float2 c0 = P.coef[P.coef_off[0] + (int64_t)j0 * P.M + i];
+        const int64_t plane = (int64_t)((k0 + j0) & (g.K[0] - 1)) * g.Kstride[0];
+        float2 acc1 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j1 = 0; j1 < (JF > 0 ? JF : kMaxJ); ++j1) {
+          if (JF == 0 && j1 >= J1) break;
+          const int64_t row = plane + (int64_t)((k1 + j1) & (g.K[1] - 1)) * g.Kstride[1];
+          acc1 = cadd(acc1, cmul(c1v[j1], __ldg(&grid[row + gl])));
+        }
+        acc = cadd(acc, cmul(c0, acc1));
+      }
+      part = cmul(cl, acc);
+    }
+  }
+  // Sum the G partial values of each lane group (fixed order: lane base .. base+G-1).
+  const int base = sub * G;
+  float2 tot = make_float2(0.f, 0.f);
+  for (int q = 0; q < G; ++q) {
+    const int src = (base + q) & 31;
+    tot.x += __shfl_sync(0xffffffffu, part.x, src);
+    tot.y += __shfl_sync(0xffffffffu, part.y, src);
+  }
+  if (active && l == 0) y[P.perm[i]] = tot;
+}
+
+// ---------------------------------------------------------------- gridding, per chunk
+template <int D, int JF>
+__global__ void __launch_bounds__(256)
+k_gridding_chunk(const float2* __restrict__ y, float2* __restrict__ tiles, const Chunk* __restrict__ chunks,
+                 const Points P, const Geom g) {
+  extern __shared__ float2 tile[];
+  const Chunk ch = chunks[blockIdx.x];
+  float* tf = reinterpret_cast<float*>(tile);
+  for (int64_t c = threadIdx.x; c < g.padded_cells; c += blockDim.x) tile[c] = make_float2(0.f, 0.f);
+  __syncthreads();
+
+  // tile origin of this chunk's bin
+  int org[kMaxDim];
+  {
+    int rem = ch.bin;
+    for (int a = D - 1; a >= 0; --a) {
+      org[a] = (rem % g.nb[a]) * g.T[a];
+      rem /= g.nb[a];
+    }
+  }
+  const int G = JF > 0 ? JF : g.J[D - 1];
+  const int lane = threadIdx.x & 31;
+  const int per_warp = 32 / G;
+  const int sub = lane / G;
+  const int l = lane - sub * G;
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const int P0 = g.P[0];
+  const int P1 = D > 1 ? g.P[1] : 1;
+  const int P2 = D > 2 ? g.P[2] : 1;
+  (void)P0;
+
+  if (sub < per_warp) {
+    for (int q = warp * per_warp + sub; q < ch.count; q += nwarps * per_warp) {
+      const int64_t i = (int64_t)ch.start + q;
+      const float2 yv = __ldg(&y[P.perm[i]]);
+      const int ll = P.kf[(int64_t)(D - 1) * P.M + i] - org[D - 1] + l;
+      const float2 cl = P.coef[P.coef_off[D - 1] + (int64_t)l * P.M + i];
+      const float2 yl = cmulc(cl, yv);  // conj(c_last) * y
+      if (D == 1) {
+        atomicAdd(&tf[2 * ll], yl.x);
+        atomicAdd(&tf[2 * ll + 1], yl.y);
+      } else if (D == 2) {
+        const int l0 = P.kf[i] - org[0];
+        const int J0 = JF > 0 ? JF : g.J[0];
+#pragma unroll
+        for (int j0 = 0; j0 < (JF > 0 ? JF : kMaxJ); ++j0) {
+          if (JF == 0 && j0 >= J0) break;
+          const float2 c0 = P.coef[P.coef_off[0] + (int64_t)j0 * P.M + i];
+          const float2 w = cmulc(c0, yl);
+          const int cell = (l0 + j0) * P1 + ll;
+          atomicAdd(&tf[2 * cell], w.x);
+          atomicAdd(&tf[2 * cell + 1], w.y);
+        }
+      } else {
+        const int l0 = P.kf[i] - org[0];
+        const int l1 = P.kf[P.M + i] - org[1];
+        const int J0 = JF > 0 ? JF : g.J[0];
+        const int J1 = JF > 0 ? JF : g.J[1];
+        float2 c1v[JF > 0 ? JF : kMaxJ];
+#pragma unroll
+        for (int j1 = 0; j1 < (JF > 0 ? JF : kMaxJ); ++j1) {
+          if (JF == 0 && j1 >= J1) break;
+          c1v[j1] = P.coef[P.coef_off[1] + (int64_t)j1 * P.M + i];
+        }
+#pragma unroll 1
+        for (int j0 = 0; j0 < J0; ++j0) {
+          const float2 c0 = P.coef[P.coef_off[0] + (int64_t)j0 * P.M + i];
+          const float2 w0 = cmulc(c0, yl);
+#pragma unroll
+          for (int j1 = 0; j1 < (JF > 0 ? JF : kMaxJ); ++j1) {
+            if (JF == 0 && j1 >= J1) break;
+            const float2 w = cmulc(c1v[j1], w0);
+            const int cell = ((l0 + j0) * P1 + (l1 + j1)) * P2 + ll;
+            atomicAdd(&tf[2 * cell], w.x);
+            atomicAdd(&tf[2 * cell + 1], w.y);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  float2* out = tiles + (int64_t)blockIdx.x * g.padded_cells;
+  for (int64_t c = threadIdx.x; c < g.padded_cells; c += blockDim.x) out[c] = tile[c];
+}
+
+// ---------------------------------------------------------------- gridding, tile reduction
+// One CTA per tile: grid cell c of tile b is the sum over e in {0,1}^d of the
+// padded tiles of bin b - e (wrapped per dimension) at local position
+// c - origin(b) + e * T, when that position lies inside the padded tile.
+template <int D>
+__global__ void __launch_bounds__(256)
+k_gridding_reduce(const float2* __restrict__ tiles, const int32_t* __restrict__ bin_chunk,
+                  float2* __restrict__ grid, const Geom g) {
+  const int64_t bin = blockIdx.x;
+  int bc[kMaxDim];
+  {
+    int64_t rem = bin;
+    for (int a = D - 1; a >= 0; --a) {
+      bc[a] = (int)(rem % g.nb[a]);
+      rem /= g.nb[a];
+    }
+  }
+  int64_t tile_cells = 1;
+  for (int a = 0; a < D; ++a) tile_cells *= g.T[a];
+  for (int64_t c = threadIdx.x; c < tile_cells; c += blockDim.x) {
+    int lc[kMaxDim];
+    {
+      int64_t rem = c;
+      for (int a = D - 1; a >= 0; --a) {
+        lc[a] = (int)(rem % g.T[a]);
+        rem /= g.T[a];
+      }
+    }
+    float2 acc = make_float2(0.f, 0.f);
+    for (int e = 0; e < (1 << D); ++e) {
+      int64_t src_bin = 0;
+      int64_t loc = 0;
+      bool ok = true;
+      for (int a = 0; a < D; ++a) {
+        const int ea = (e >> (D - 1 - a)) & 1;
+        const int la = lc[a] + ea * g.T[a];
+        if (la >= g.P[a]) { ok = false; break; }
+        const int ba = (bc[a] - ea + g.nb[a]) % g.nb[a];
+        src_bin = src_bin * g.nb[a] + ba;
+        loc = loc * g.P[a] + la;
+      }
+      if (!ok) continue;
+      const int q0 = bin_chunk[src_bin], q1 = bin_chunk[src_bin + 1];
+      for (int q = q0; q < q1; ++q) acc = cadd(acc, __ldg(&tiles[(int64_t)q * g.padded_cells + loc]));
+    }
+    int64_t off = 0;
+    for (int a = 0; a < D; ++a) off += (int64_t)(bc[a] * g.T[a] + lc[a]) * g.Kstride[a];
+    grid[off] = acc;
+  }
+}
+
+bool all_j_equal(const Geom& g, int J) {
+  for (int a = 0; a < g.d; ++a)
+    if (g.J[a] != J) return false;
+  return true;
+}
+
+template <int D>
+cudaError_t interp_d(const nufft_plan_t* p, const float2* grid, float2* y) {
+  const Points P = points_view(p);
+  const int G = p->g.J[D - 1];
+  const int per_warp = 32 / G;
+  const int64_t warps = (P.M + per_warp - 1) / per_warp;
+  const int64_t blocks = (warps * 32 + 255) / 256;
+  if (blocks == 0) return cudaSuccess;
+  if (all_j_equal(p->g, 6)) k_interp<D, 6><<<(unsigned)blocks, 256, 0, p->stream>>>(grid, y, P, p->g);
+  else k_interp<D, 0><<<(unsigned)blocks, 256, 0, p->stream>>>(grid, y, P, p->g);
+  return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t gridding_d(const nufft_plan_t* p, const float2* y, float2* grid) {
+  const Points P = points_view(p);
+  const size_t smem = (size_t)p->g.padded_cells * sizeof(float2);
+  if (p->nchunks > 0) {
+    if (all_j_equal(p->g, 6)) {
+      cudaError_t e = cudaFuncSetAttribute(k_gridding_chunk<D, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k_gridding_chunk<D, 6><<<(unsigned)p->nchunks, 256, smem, p->stream>>>(y, p->tiles, p->chunks, P, p->g);
+    } else {
+      cudaError_t e = cudaFuncSetAttribute(k_gridding_chunk<D, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k_gridding_chunk<D, 0><<<(unsigned)p->nchunks, 256, smem, p->stream>>>(y, p->tiles, p->chunks, P, p->g);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  k_gridding_reduce<D><<<(unsigned)p->g.nbins, 256, 0, p->stream>>>(p->tiles, p->bin_chunk, grid, p->g);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int launch_interp(nufft_plan_t* p, const float2* grid, float2* y) {
+  cudaError_t e;
+  switch (p->g.d) {
+    case 1: e = interp_d<1>(p, grid, y); break;
+    case 2: e = interp_d<2>(p, grid, y); break;
+    default: e = interp_d<3>(p, grid, y); break;
+  }
+  return e == cudaSuccess ? NUFFT_OK : cuda_check(p, e, "interpolation kernel");
+}
+
+int launch_gridding(nufft_plan_t* p, const float2* y, float2* grid) {
+  cudaError_t e;
+  switch (p->g.d) {
+    case 1: e = gridding_d<1>(p, y, grid); break;
+    case 2: e = gridding_d<2>(p, y, grid); break;
+    default: e = gridding_d<3>(p, y, grid); break;
+  }
+  return e == cudaSuccess ? NUFFT_OK : cuda_check(p, e, "gridding kernels");
+}
+
+}  // namespace nufft

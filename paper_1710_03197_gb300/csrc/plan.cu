@@ -1,0 +1,624 @@
+// plan.cu - plan creation: FP64 min-max interpolator precompute on the GPU,
+// tile sort of the trajectory, work lists and plan-owned buffers.
+//
+// Section 2.1 (the min-max kernel of Fessler and Sutton is PyNUFFT's default)
+// and Section 2.1.3 (the interpolator is precomputed once; the paper stores it
+// as a CSR matrix).  Section 2.2.3 offloads its pre-indexes before the
+// iterations start; the plan likewise does all index work once.
+//
+// Interpolator (one dimension; t_n = n - N/2, gamma = 2 pi / K):
+//   s_n   = z_n / sinh(z_n), z_n = sqrt(alpha^2 - (pi J t_n / K)^2), alpha = 2.34 J
+//           (sin for a negative radicand), normalised to max_n s_n = 1;
+//   G     = [sum_n s_n^2 exp(i gamma (j - j') t_n)]_{j,j'=1..J},  T = G^{-1};
+//   k0    = floor(w / gamma) - J/2 (J even), floor(w / gamma + 1/2) - (J+1)/2 (J odd);
+//   r_j   = sum_n s_n exp(-i (w - gamma (k0 + j)) t_n),  c = T r.
+// c minimises the worst-case interpolation error over unit-norm images (the
+// least-squares solution of the min-max problem); the d-dimensional weight is
+// the product of the per-dimension c.  All of it is computed in FP64 and the
+// coefficients are stored as complex64.
+#include <cmath>
+#include <cstdarg>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace nufft {
+
+static thread_local char g_err[512] = "no error";
+
+int set_error(nufft_plan_t* p, int code, const char* fmt, ...) {
+  char* dst = p ? p->err : g_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 512, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_check(nufft_plan_t* p, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return NUFFT_OK;
+  if (e == cudaErrorMemoryAllocation)
+    return set_error(p, NUFFT_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+  return set_error(p, NUFFT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+Points points_view(const nufft_plan_t* p) {
+  Points P;
+  P.M = p->M;
+  P.kf = p->kf;
+  P.coef = p->coef;
+  for (int a = 0; a < kMaxDim; ++a) P.coef_off[a] = p->coef_off[a];
+  P.perm = p->perm;
+  return P;
+}
+
+namespace {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+// ---------------------------------------------------------------- per-dimension tables
+struct DimTables {
+  int d;
+  int N[kMaxDim], K[kMaxDim], J[kMaxDim];
+  int64_t s_off[kMaxDim];     // into s (float) and s64 (double)
+  int64_t tw_off[kMaxDim];
+  int64_t T_off[kMaxDim];     // into Tinv (double2), J*J each
+};
+
+__device__ double kb_recip_ft(double t, int J, int K) {
+  const double alpha = 2.34 * J;
+  const double q = alpha * alpha - (kPi * J * t / K) * (kPi * J * t / K);
+  double ft;
+  if (q > 0.0) {
+    const double z = sqrt(q);
+    ft = sinh(z) / z;
+  } else if (q < 0.0) {
+    const double z = sqrt(-q);
+    ft = sin(z) / z;
+  } else {
+    ft = 1.0;
+  }
+  return 1.0 / ft;
+}
+
+// One CTA per dimension: scaling factors (max-normalised) and twiddles.
+__global__ void k_scaling_twiddle(DimTables D, float* s, double* s64, float2* tw) {
+  const int a = blockIdx.x;
+  const int N = D.N[a], K = D.K[a], J = D.J[a];
+  __shared__ double red[256];
+  double mx = 0.0;
+  for (int n = threadIdx.x; n < N; n += blockDim.x) {
+    const double v = kb_recip_ft((double)n - 0.5 * N, J, K);
+    s64[D.s_off[a] + n] = v;
+    mx = fmax(mx, v);
+  }
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  const double smax = red[0];
+  for (int n = threadIdx.x; n < N; n += blockDim.x) {
+    const double v = s64[D.s_off[a] + n] / smax;
+    s64[D.s_off[a] + n] = v;
+    s[D.s_off[a] + n] = (float)v;
+  }
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double sn, cs;
+    sincospi(-2.0 * (double)k / (double)K, &sn, &cs);
+    tw[D.tw_off[a] + k] = make_float2((float)cs, (float)sn);
+  }
+}
+
+// One CTA per dimension: G (J x J, Hermitian) and its inverse by Gauss-Jordan
+// elimination with partial pivoting, in FP64.
+__global__ void k_minmax_T(DimTables D, const double* s64, double2* Tinv, int* singular) {
+  const int a = blockIdx.x;
+  const int N = D.N[a], K = D.K[a], J = D.J[a];
+  const double gamma = 2.0 * kPi / K;
+  __shared__ double2 Aug[kMaxJ][2 * kMaxJ];
+  for (int e = threadIdx.x; e < J * J; e += blockDim.x) {
+    const int r = e / J, c = e % J;
+    double re = 0.0, im = 0.0;
+    for (int n = 0; n < N; ++n) {
+      const double sv = s64[D.s_off[a] + n];
+      double sn, cs;
+      sincos(gamma * (double)(r - c) * ((double)n - 0.5 * N), &sn, &cs);
+      re += sv * sv * cs;
+      im += sv * sv * sn;
+    }
+    Aug[r][c] = make_double2(re, im);
+    Aug[r][J + c] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int col = 0; col < J; ++col) {
+      int piv = col;
+      double best = -1.0;
+      for (int r = col; r < J; ++r) {
+        const double m = Aug[r][col].x * Aug[r][col].x + Aug[r][col].y * Aug[r][col].y;
+        if (m > best) { best = m; piv = r; }
+      }
+      if (best <= 0.0) { *singular = 1; return; }
+      if (piv != col)
+        for (int c = 0; c < 2 * J; ++c) { double2 t = Aug[col][c]; Aug[col][c] = Aug[piv][c]; Aug[piv][c] = t; }
+      // scale the pivot row by 1 / pivot
+      const double2 pv = Aug[col][col];
+      const double den = pv.x * pv.x + pv.y * pv.y;
+      const double2 inv = make_double2(pv.x / den, -pv.y / den);
+      for (int c = 0; c < 2 * J; ++c) {
+        const double2 v = Aug[col][c];
+        Aug[col][c] = make_double2(v.x * inv.x - v.y * inv.y, v.x * inv.y + v.y * inv.x);
+      }
+      for (int r = 0; r < J; ++r) {
+        if (r == col) continue;
+        const double2 f = Aug[r][col];
+        for (int c = 0; c < 2 * J; ++c) {
+          const double2 v = Aug[col][c];
+          Aug[r][c].x -= f.x * v.x - f.y * v.y;
+          Aug[r][c].y -= f.x * v.y + f.y * v.x;
+        }
+      }
+    }
+    for (int r = 0; r < J; ++r)
+      for (int c = 0; c < J; ++c) Tinv[D.T_off[a] + r * J + c] = Aug[r][J + c];
+  }
+}
+
+// floor-based first offset k0 (FP64), shared by the binning and coefficient kernels.
+__device__ __forceinline__ double offset_k0(double w, int K, int J) {
+  const double gamma = (2.0 * kPi) / K;
+  const double u = w / gamma;
+  return (J & 1) ? floor(u + 0.5) - (double)((J + 1) / 2) : floor(u) - (double)(J / 2);
+}
+
+__device__ __forceinline__ int wrap_first(double k0, int K) {
+  // first neighbour k0 + 1, wrapped into [0, K)
+  const long long k = (long long)k0 + 1;
+  long long r = k % K;
+  if (r < 0) r += K;
+  return (int)r;
+}
+
+__global__ void k_validate(const float* om, int64_t n, int* bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = om[i];
+    if (!(fabsf(v) <= 1048576.0f)) atomicOr(bad, 1);  // also catches NaN
+  }
+}
+
+__global__ void k_bins(const float* om, int64_t M, Geom g, uint32_t* key, int32_t* val) {
+  const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  uint32_t bin = 0;
+  for (int a = 0; a < g.d; ++a) {
+    const int kf = wrap_first(offset_k0((double)om[m * g.d + a], g.K[a], g.J[a]), g.K[a]);
+    bin = bin * g.nb[a] + kf / g.T[a];
+  }
+  key[m] = bin;
+  val[m] = (int32_t)m;
+}
+
+// ---------------------------------------------------------------- stable LSD radix sort (8 bits/pass)
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 4096;  // items per CTA
+
+__global__ void k_radix_hist(const uint32_t* key, int64_t n, int shift, int nblk, uint32_t* hist) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t lo = (int64_t)blockIdx.x * kSortItems;
+  const int64_t hi = min(n, lo + kSortItems);
+  for (int64_t i = lo + threadIdx.x; i < hi; i += kSortThreads) atomicAdd(&h[(key[i] >> shift) & 255u], 1u);
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan of n values with a single CTA of 1024 threads, in place
+__global__ void k_scan_exclusive(uint32_t* v, int64_t n) {
+  __shared__ uint32_t part[1024];
+  const int64_t per = (n + 1023) / 1024;
+  const int64_t lo = threadIdx.x * per;
+  const int64_t hi = min(n, lo + per);
+  uint32_t s = 0;
+  for (int64_t i = lo; i < hi; ++i) s += v[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int t = 0; t < 1024; ++t) { const uint32_t c = part[t]; part[t] = run; run += c; }
+  }
+  __syncthreads();
+  uint32_t run = part[threadIdx.x];
+  for (int64_t i = lo; i < hi; ++i) { const uint32_t c = v[i]; v[i] = run; run += c; }
+}
+
+// Stable scatter: items of a CTA are ranked in their original order.
+__global__ void k_radix_scatter(const uint32_t* kin, const int32_t* vin, uint32_t* kout, int32_t* vout,
+                                int64_t n, int shift, int nblk, const uint32_t* offs) {
+  __shared__ uint32_t running[256];
+  __shared__ uint32_t wcount[kSortThreads / 32][256];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  running[tid] = offs[(int64_t)tid * nblk + blockIdx.x];
+  const int64_t lo = (int64_t)blockIdx.x * kSortItems;
+  for (int round = 0; round < kSortItems / kSortThreads; ++round) {
+    for (int w = 0; w < kSortThreads / 32; ++w) wcount[w][tid] = 0;
+    __syncthreads();
+    const int64_t i = lo + (int64_t)round * kSortThreads + tid;
+    const bool valid = i < n;
+    const uint32_t k = valid ? kin[i] : 0u;
+    const uint32_t digit = valid ? ((k >> shift) & 255u) : 256u;
+    const unsigned peers = __match_any_sync(0xffffffffu, digit);
+    const unsigned lt = (1u << lane) - 1u;
+    const int rank_w = __popc(peers & lt);
+    if (valid && rank_w == 0) wcount[warp][digit] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      uint32_t before = 0;
+      for (int w = 0; w < warp; ++w) before += wcount[w][digit];
+      const uint32_t pos = running[digit] + before + rank_w;
+      kout[pos] = k;
+      vout[pos] = vin[i];
+    }
+    __syncthreads();
+    uint32_t tot = 0;
+    for (int w = 0; w < kSortThreads / 32; ++w) tot += wcount[w][tid];
+    running[tid] += tot;
+    __syncthreads();
+  }
+}
+
+// bin_start[b] = first sorted position with key >= b (binary search), b = 0..nbins
+__global__ void k_bin_start(const uint32_t* key, int64_t M, int64_t nbins, int32_t* bin_start) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b > nbins) return;
+  int64_t lo = 0, hi = M;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)key[mid] < b) lo = mid + 1; else hi = mid;
+  }
+  bin_start[b] = (int32_t)lo;
+}
+
+// Per sorted point and dimension: first neighbour and the J min-max coefficients.
+__global__ void k_coefficients(const float* om, Geom g, int64_t M, const int32_t* perm, const double* s64,
+                               DimTables D, const double2* Tinv, int32_t* kf_out, float2* coef,
+                               int64_t coef_off0, int64_t coef_off1, int64_t coef_off2) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= M * g.d) return;
+  const int a = (int)(idx / M);
+  const int64_t i = idx - (int64_t)a * M;
+  const int64_t m = perm[i];
+  const int N = g.N[a], K = g.K[a], J = g.J[a];
+  const double w = (double)om[m * g.d + a];
+  const double k0 = offset_k0(w, K, J);
+  const double gamma = (2.0 * kPi) / K;
+  const double* s = s64 + D.s_off[a];
+  double2 r[kMaxJ];
+  for (int j = 1; j <= J; ++j) {
+    // r_j = sum_n s_n exp(-i theta t_n), theta = w - gamma (k0 + j), t_n = n - N/2,
+    // accumulated with the rotation exp(-i theta) from exp(+i theta N/2).
+    const double theta = w - gamma * (k0 + (double)j);
+    double sn, cs;
+    sincos(-theta, &sn, &cs);            // rotation per step
+    double es, ec;
+    sincos(theta * 0.5 * N, &es, &ec);   // value at n = 0 (t = -N/2)
+    double re = 0.0, im = 0.0;
+    for (int n = 0; n < N; ++n) {
+      re += s[n] * ec;
+      im += s[n] * es;
+      const double nc = ec * cs - es * sn;
+      const double ns = ec * sn + es * cs;
+      ec = nc;
+      es = ns;
+    }
+    r[j - 1] = make_double2(re, im);
+  }
+  const double2* T = Tinv + D.T_off[a];
+  const int64_t off = a == 0 ? coef_off0 : (a == 1 ? coef_off1 : coef_off2);
+  for (int j = 0; j < J; ++j) {
+    double re = 0.0, im = 0.0;
+    for (int q = 0; q < J; ++q) {
+      const double2 t = T[j * J + q];
+      re += t.x * r[q].x - t.y * r[q].y;
+      im += t.x * r[q].y + t.y * r[q].x;
+    }
+    coef[off + (int64_t)j * M + i] = make_float2((float)re, (float)im);
+  }
+  kf_out[(int64_t)a * M + i] = wrap_first(k0, K);
+}
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+template <class T>
+cudaError_t dalloc(nufft_plan_t* p, T** ptr, int64_t count) {
+  *ptr = nullptr;
+  if (count <= 0) return cudaSuccess;
+  const size_t bytes = (size_t)count * sizeof(T);
+  cudaError_t e = cudaMalloc((void**)ptr, bytes);
+  if (e == cudaSuccess) p->device_bytes += (int64_t)bytes;
+  return e;
+}
+
+void free_plan_memory(nufft_plan_t* p) {
+  void* bufs[] = {p->s, p->twiddle, p->kf, p->coef, p->perm, p->bin_start, p->chunks, p->bin_chunk,
+                  p->tiles, p->grid, p->ytmp, p->x_stage, p->y_stage, p->solver_ws};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+}
+
+int build_plan(nufft_plan_t* p, const float* om) {
+  Geom& g = p->g;
+  const int d = g.d;
+  const int64_t M = p->M;
+  cudaStream_t st = p->stream;
+  int rc;
+
+  // ---- validate om on the device
+  int* flag = nullptr;
+  NUFFT_CUDA_TRY(p, cudaMalloc((void**)&flag, 2 * sizeof(int)));
+  struct FlagGuard { int* f; ~FlagGuard() { if (f) cudaFree(f); } } fg{flag};
+  NUFFT_CUDA_TRY(p, cudaMemsetAsync(flag, 0, 2 * sizeof(int), st));
+  if (M > 0) {
+    const int64_t n = M * d;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    k_validate<<<blocks, 256, 0, st>>>(om, n, flag);
+    NUFFT_CUDA_TRY(p, cudaGetLastError());
+  }
+  int hflag[2] = {0, 0};
+  NUFFT_CUDA_TRY(p, cudaMemcpyAsync(hflag, flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  NUFFT_CUDA_TRY(p, cudaStreamSynchronize(st));
+  if (hflag[0]) return set_error(p, NUFFT_EINVAL, "om holds a non-finite value or |om| > 2^20");
+
+  // ---- per-dimension tables
+  DimTables D;
+  memset(&D, 0, sizeof(D));
+  D.d = d;
+  int64_t s_tot = 0, tw_tot = 0, T_tot = 0;
+  for (int a = 0; a < d; ++a) {
+    D.N[a] = g.N[a]; D.K[a] = g.K[a]; D.J[a] = g.J[a];
+    D.s_off[a] = s_tot; D.tw_off[a] = tw_tot; D.T_off[a] = T_tot;
+    p->s_off[a] = s_tot; p->tw_off[a] = tw_tot;
+    s_tot += g.N[a]; tw_tot += g.K[a]; T_tot += (int64_t)g.J[a] * g.J[a];
+  }
+  double* s64 = nullptr;
+  double2* Tinv = nullptr;
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->s, s_tot));
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->twiddle, tw_tot));
+  NUFFT_CUDA_TRY(p, cudaMalloc((void**)&s64, s_tot * sizeof(double)));
+  struct Tmp { void* a; void* b; void* c; void* d; void* e; ~Tmp() { for (void* v : {a, b, c, d, e}) if (v) cudaFree(v); } } tmp{s64, nullptr, nullptr, nullptr, nullptr};
+  NUFFT_CUDA_TRY(p, cudaMalloc((void**)&Tinv, T_tot * sizeof(double2)));
+  tmp.b = Tinv;
+  k_scaling_twiddle<<<d, 256, 0, st>>>(D, p->s, s64, p->twiddle);
+  NUFFT_CUDA_TRY(p, cudaGetLastError());
+  k_minmax_T<<<d, 256, 0, st>>>(D, s64, Tinv, flag + 1);
+  NUFFT_CUDA_TRY(p, cudaGetLastError());
+
+  // ---- binning and stable sort by tile
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->perm, M));
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->bin_start, g.nbins + 1));
+  uint32_t *keyA = nullptr, *keyB = nullptr, *hist = nullptr;
+  int32_t* valB = nullptr;
+  if (M > 0) {
+    NUFFT_CUDA_TRY(p, cudaMalloc((void**)&keyA, M * sizeof(uint32_t)));
+    tmp.c = keyA;
+    NUFFT_CUDA_TRY(p, cudaMalloc((void**)&keyB, M * sizeof(uint32_t)));
+    tmp.d = keyB;
+    NUFFT_CUDA_TRY(p, cudaMalloc((void**)&valB, M * sizeof(int32_t)));
+    tmp.e = valB;
+    k_bins<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(om, M, g, keyA, p->perm);
+    NUFFT_CUDA_TRY(p, cudaGetLastError());
+    const int nblk = (int)((M + kSortItems - 1) / kSortItems);
+    NUFFT_CUDA_TRY(p, cudaMalloc((void**)&hist, (size_t)256 * nblk * sizeof(uint32_t)));
+    struct HG { void* h; ~HG() { if (h) cudaFree(h); } } hg{hist};
+    int bits = 0;
+    while ((int64_t(1) << bits) < g.nbins) ++bits;
+    const int passes = std::max(1, (bits + 7) / 8);
+    uint32_t* kin = keyA; uint32_t* kout = keyB;
+    int32_t* vin = p->perm; int32_t* vout = valB;
+    for (int pass = 0; pass < passes; ++pass) {
+      k_radix_hist<<<nblk, kSortThreads, 0, st>>>(kin, M, 8 * pass, nblk, hist);
+      k_scan_exclusive<<<1, 1024, 0, st>>>(hist, (int64_t)256 * nblk);
+      k_radix_scatter<<<nblk, kSortThreads, 0, st>>>(kin, vin, kout, vout, M, 8 * pass, nblk, hist);
+      NUFFT_CUDA_TRY(p, cudaGetLastError());
+      std::swap(kin, kout);
+      std::swap(vin, vout);
+    }
+    if (vin != p->perm)
+      NUFFT_CUDA_TRY(p, cudaMemcpyAsync(p->perm, vin, M * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    k_bin_start<<<(unsigned)((g.nbins + 1 + 255) / 256), 256, 0, st>>>(kin, M, g.nbins, p->bin_start);
+    NUFFT_CUDA_TRY(p, cudaGetLastError());
+    NUFFT_CUDA_TRY(p, cudaStreamSynchronize(st));
+  } else {
+    NUFFT_CUDA_TRY(p, cudaMemsetAsync(p->bin_start, 0, (g.nbins + 1) * sizeof(int32_t), st));
+  }
+
+  // ---- per-point interpolator in sorted order
+  int64_t coef_tot = 0;
+  for (int a = 0; a < d; ++a) { p->coef_off[a] = coef_tot; coef_tot += (int64_t)g.J[a] * M; }
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->kf, M * d));
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->coef, coef_tot));
+  if (M > 0) {
+    const int64_t n = M * d;
+    k_coefficients<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(om, g, M, p->perm, s64, D, Tinv, p->kf, p->coef,
+                                                               p->coef_off[0], p->coef_off[1], p->coef_off[2]);
+    NUFFT_CUDA_TRY(p, cudaGetLastError());
+  }
+  NUFFT_CUDA_TRY(p, cudaMemcpyAsync(hflag, flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  NUFFT_CUDA_TRY(p, cudaStreamSynchronize(st));
+  if (hflag[1]) return set_error(p, NUFFT_EINVAL, "min-max matrix G is singular for these sizes");
+
+  // ---- gridding work list: each tile's points cut into chunks
+  std::vector<int32_t> bs(g.nbins + 1);
+  NUFFT_CUDA_TRY(p, cudaMemcpy(bs.data(), p->bin_start, (g.nbins + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  std::vector<Chunk> ch;
+  std::vector<int32_t> bc(g.nbins + 1);
+  for (int64_t b = 0; b < g.nbins; ++b) {
+    bc[b] = (int32_t)ch.size();
+    for (int32_t s0 = bs[b]; s0 < bs[b + 1]; s0 += kChunkPoints) {
+      Chunk c;
+      c.bin = (int32_t)b;
+      c.start = s0;
+      c.count = std::min<int32_t>(kChunkPoints, bs[b + 1] - s0);
+      c.pad = 0;
+      ch.push_back(c);
+    }
+  }
+  bc[g.nbins] = (int32_t)ch.size();
+  p->nchunks = (int64_t)ch.size();
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->chunks, p->nchunks));
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->bin_chunk, g.nbins + 1));
+  if (p->nchunks > 0)
+    NUFFT_CUDA_TRY(p, cudaMemcpy(p->chunks, ch.data(), ch.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
+  NUFFT_CUDA_TRY(p, cudaMemcpy(p->bin_chunk, bc.data(), bc.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+
+  // ---- work space
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->tiles, p->nchunks * g.padded_cells));
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->grid, p->Kprod));
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->ytmp, M));
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->x_stage, p->Nprod));
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->y_stage, M));
+  rc = NUFFT_OK;
+  return rc;
+}
+
+}  // namespace
+}  // namespace nufft
+
+using namespace nufft;
+
+extern "C" int nufft_plan(int d, const int* Nd, const int* Kd, const int* Jd, int64_t M, const float* om_dev,
+                          void* stream, nufft_plan_t** out) {
+  if (!out) return set_error(nullptr, NUFFT_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (d < 1 || d > kMaxDim) return set_error(nullptr, NUFFT_EINVAL, "d = %d, must be 1..3", d);
+  if (!Nd || !Kd || !Jd) return set_error(nullptr, NUFFT_EINVAL, "Nd, Kd and Jd must not be NULL");
+  if (M < 0 || M > 2147483647LL) return set_error(nullptr, NUFFT_EINVAL, "M = %lld out of range", (long long)M);
+  if (M > 0 && !om_dev) return set_error(nullptr, NUFFT_EINVAL, "om_dev is NULL with M > 0");
+  Geom g;
+  memset(&g, 0, sizeof(g));
+  g.d = d;
+  const int base_tile = d == 1 ? 1024 : (d == 2 ? 32 : 16);
+  for (int a = 0; a < d; ++a) {
+    const int N = Nd[a], K = Kd[a], J = Jd[a];
+    if (!is_pow2(K) || K < kMinK || K > kMaxK)
+      return set_error(nullptr, NUFFT_EINVAL, "K[%d] = %d must be a power of two in [%d, %d]", a, K, kMinK, kMaxK);
+    if (N < 2 || (N & 1) || N > K)
+      return set_error(nullptr, NUFFT_EINVAL, "N[%d] = %d must be even with 2 <= N <= K = %d", a, N, K);
+    if (J < 1 || J > kMaxJ || J > K)
+      return set_error(nullptr, NUFFT_EINVAL, "J[%d] = %d must satisfy 1 <= J <= min(16, K)", a, J);
+    g.N[a] = N; g.K[a] = K; g.J[a] = J;
+    g.T[a] = std::min(base_tile, K);
+    g.nb[a] = K / g.T[a];
+    g.P[a] = g.T[a] + J - 1;
+  }
+  int64_t stride = 1;
+  g.nbins = 1;
+  g.padded_cells = 1;
+  for (int a = d - 1; a >= 0; --a) {
+    g.Kstride[a] = stride;
+    stride *= g.K[a];
+    g.nbins *= g.nb[a];
+    g.padded_cells *= g.P[a];
+  }
+  if (g.padded_cells * (int64_t)sizeof(float2) > 200 * 1024)
+    return set_error(nullptr, NUFFT_EINVAL, "padded gridding tile of %lld cells exceeds shared memory; lower J",
+                     (long long)g.padded_cells);
+  if (g.nbins > 65536) return set_error(nullptr, NUFFT_EINVAL, "too many tiles (%lld)", (long long)g.nbins);
+
+  nufft_plan_t* p = new (std::nothrow) nufft_plan_t;
+  if (!p) return set_error(nullptr, NUFFT_ENOMEM, "host allocation of the plan failed");
+  memset(p, 0, sizeof(*p));
+  p->g = g;
+  p->M = M;
+  p->Nprod = 1;
+  p->Kprod = 1;
+  for (int a = 0; a < d; ++a) { p->Nprod *= g.N[a]; p->Kprod *= g.K[a]; }
+  p->stream = (cudaStream_t)stream;
+  snprintf(p->err, sizeof(p->err), "no error");
+  const int rc = build_plan(p, om_dev);
+  if (rc != NUFFT_OK) {
+    set_error(nullptr, rc, "%s", p->err);
+    free_plan_memory(p);
+    delete p;
+    return rc;
+  }
+  *out = p;
+  return NUFFT_OK;
+}
+
+extern "C" int nufft_plan_destroy(nufft_plan_t* p) {
+  if (!p) return NUFFT_OK;
+  cudaStreamSynchronize(p->stream);
+  free_plan_memory(p);
+  delete p;
+  return NUFFT_OK;
+}
+
+extern "C" const char* nufft_last_error(const nufft_plan_t* p) { return p ? p->err : g_err; }
+
+extern "C" int nufft_set_stream(nufft_plan_t* p, void* stream) {
+  if (!p) return set_error(nullptr, NUFFT_EINVAL, "plan is NULL");
+  p->stream = (cudaStream_t)stream;
+  return NUFFT_OK;
+}
+
+extern "C" int nufft_plan_info(const nufft_plan_t* p, int64_t* info) {
+  if (!p || !info) return set_error(nullptr, NUFFT_EINVAL, "plan or info is NULL");
+  for (int i = 0; i < 16; ++i) info[i] = 0;
+  info[0] = p->g.d;
+  info[1] = p->M;
+  for (int a = 0; a < p->g.d; ++a) {
+    info[2 + a] = p->g.N[a];
+    info[5 + a] = p->g.K[a];
+    info[8 + a] = p->g.J[a];
+  }
+  info[11] = p->g.nbins;
+  info[12] = p->nchunks;
+  info[13] = p->device_bytes;
+  info[14] = p->g.T[0];
+  info[15] = p->g.T[p->g.d - 1];
+  return NUFFT_OK;
+}
+
+extern "C" int nufft_plan_get_interpolator(const nufft_plan_t* cp, int32_t* kfirst_host, float* coef_host,
+                                           float* s_host, int32_t* perm_host) {
+  nufft_plan_t* p = const_cast<nufft_plan_t*>(cp);
+  if (!p) return set_error(nullptr, NUFFT_EINVAL, "plan is NULL");
+  const int d = p->g.d;
+  const int64_t M = p->M;
+  NUFFT_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+  std::vector<int32_t> perm(M), kf(M * d);
+  if (M > 0) {
+    NUFFT_CUDA_TRY(p, cudaMemcpy(perm.data(), p->perm, M * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    NUFFT_CUDA_TRY(p, cudaMemcpy(kf.data(), p->kf, M * d * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  }
+  if (perm_host) for (int64_t i = 0; i < M; ++i) perm_host[i] = perm[i];
+  if (kfirst_host)
+    for (int a = 0; a < d; ++a)
+      for (int64_t i = 0; i < M; ++i) kfirst_host[(int64_t)perm[i] * d + a] = kf[(int64_t)a * M + i];
+  if (coef_host && M > 0) {
+    int64_t out_off = 0;
+    for (int a = 0; a < d; ++a) {
+      const int J = p->g.J[a];
+      std::vector<float2> c((size_t)J * M);
+      NUFFT_CUDA_TRY(p, cudaMemcpy(c.data(), p->coef + p->coef_off[a], c.size() * sizeof(float2), cudaMemcpyDeviceToHost));
+      for (int64_t i = 0; i < M; ++i)
+        for (int j = 0; j < J; ++j) {
+          const float2 v = c[(size_t)j * M + i];
+          coef_host[out_off + ((int64_t)perm[i] * J + j) * 2] = v.x;
+          coef_host[out_off + ((int64_t)perm[i] * J + j) * 2 + 1] = v.y;
+        }
+      out_off += (int64_t)2 * J * M;
+    }
+  }
+  if (s_host) {
+    int64_t off = 0;
+    for (int a = 0; a < d; ++a) {
+      NUFFT_CUDA_TRY(p, cudaMemcpy(s_host + off, p->s + p->s_off[a], p->g.N[a] * sizeof(float), cudaMemcpyDeviceToHost));
+      off += p->g.N[a];
+    }
+  }
+  return NUFFT_OK;
+}

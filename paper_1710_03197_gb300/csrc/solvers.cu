@@ -1,0 +1,381 @@
+// solvers.cu - CG, L1TV-OLS and L1TV-LAD on the NUFFT normal operator.
+//
+// Section 2.1.5 (normal equation A^H A x = A^H y, Eq. 4), Section 2.2.2 (CG,
+// Eqs. 7-9), Section 2.2.3 (image gradient by rolling, Eq. 10; L1TV-OLS,
+// Eqs. 11-20; L1TV-LAD, Eqs. 21-31).  Bulk arithmetic is FP32; the inner
+// products that set the CG step lengths are accumulated in FP64 in a fixed
+// order (per-thread strided sums, a fixed shared-memory tree per CTA, then one
+// CTA summing the per-CTA results), so a solve is reproducible for a given
+// operator output.  Scalars stay in device memory: no host round trip per
+// iteration.
+#include <vector>
+
+#include "internal.cuh"
+
+namespace nufft {
+int selfadjoint_impl(nufft_plan_t* p, const float2* x, float2* out);
+int adjoint_dev(nufft_plan_t* p, const float2* y, float2* x);
+}  // namespace nufft
+
+using namespace nufft;
+
+namespace {
+
+constexpr int kDotBlocks = 608;      // 4 x 152 SMs
+constexpr int kDotThreads = 256;
+constexpr int kEwThreads = 256;
+
+// scalar slots in device memory
+enum { S_RR0 = 0, S_RR1 = 1, S_PQ = 2, S_NSLOTS = 8 };
+
+enum { V_B = 0, V_R, V_P, V_Q, V_AHY, V_AHYK, V_RHS, V_T, V_DF, V_BF, V_D0, V_B0 = V_D0 + 3, V_COUNT = V_B0 + 3 };
+
+struct Ws {
+  float2* v[V_COUNT];
+  double* part;   // [kDotBlocks]
+  double* sc;     // [S_NSLOTS]
+};
+
+int get_ws(nufft_plan_t* p, Ws* w) {
+  const int64_t n = p->Nprod;
+  const int64_t vec_bytes = ((n * (int64_t)sizeof(float2) + 255) / 256) * 256;
+  const int64_t bytes = vec_bytes * V_COUNT + (int64_t)(kDotBlocks + S_NSLOTS) * sizeof(double);
+  if (!p->solver_ws) {
+    cudaError_t e = cudaMalloc(&p->solver_ws, bytes);
+    if (e != cudaSuccess) { p->solver_ws = nullptr; return cuda_check(p, e, "solver work space"); }
+    p->solver_ws_bytes = bytes;
+    p->device_bytes += bytes;
+  }
+  char* base = (char*)p->solver_ws;
+  for (int i = 0; i < V_COUNT; ++i) w->v[i] = (float2*)(base + vec_bytes * i);
+  w->part = (double*)(base + vec_bytes * V_COUNT);
+  w->sc = w->part + kDotBlocks;
+  return NUFFT_OK;
+}
+
+// --------------------------------------------------------------- reductions
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[kDotThreads];
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = kDotThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  return red[0];
+}
+
+// part[b] = sum over this CTA's strided share of Re(conj(a) b)
+__global__ void __launch_bounds__(kDotThreads) k_dot_partial(const float2* a, const float2* b, int64_t n, double* part) {
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < n; i += (int64_t)kDotBlocks * kDotThreads) {
+    const float2 u = a[i], v = b[i];
+    s += (double)u.x * (double)v.x + (double)u.y * (double)v.y;
+  }
+  const double t = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kDotThreads) k_dot_final(const double* part, double* dst) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < kDotBlocks; i += kDotThreads) s += part[i];
+  const double t = block_sum(s);
+  if (threadIdx.x == 0) *dst = t;
+}
+
+// --------------------------------------------------------------- CG vector steps
+__device__ __forceinline__ double safe_div(double a, double b) { return b != 0.0 ? a / b : 0.0; }
+
+// x += alpha p, r -= alpha q, alpha = rr / <p, q>; also the partial sums of <r, r>.
+__global__ void __launch_bounds__(kDotThreads)
+k_cg_xr(float2* x, float2* r, const float2* p, const float2* q, int64_t n, const double* sc, int rr_slot,
+        double* part) {
+  const float alpha = (float)safe_div(sc[rr_slot], sc[S_PQ]);
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < n; i += (int64_t)kDotBlocks * kDotThreads) {
+    const float2 pv = p[i], qv = q[i];
+    float2 xv = x[i], rv = r[i];
+    xv.x = fmaf(alpha, pv.x, xv.x);
+    xv.y = fmaf(alpha, pv.y, xv.y);
+    rv.x = fmaf(-alpha, qv.x, rv.x);
+    rv.y = fmaf(-alpha, qv.y, rv.y);
+    x[i] = xv;
+    r[i] = rv;
+    s += (double)rv.x * (double)rv.x + (double)rv.y * (double)rv.y;
+  }
+  const double t = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// p = r + beta p, beta = rr_new / rr_old
+__global__ void k_cg_p(float2* p, const float2* r, int64_t n, const double* sc, int new_slot, int old_slot) {
+  const float beta = (float)safe_div(sc[new_slot], sc[old_slot]);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 rv = r[i];
+    float2 pv = p[i];
+    pv.x = fmaf(beta, pv.x, rv.x);
+    pv.y = fmaf(beta, pv.y, rv.y);
+    p[i] = pv;
+  }
+}
+
+// r = b - a, p = r (initial residual) with partial sums of <r, r>
+__global__ void __launch_bounds__(kDotThreads)
+k_cg_init(float2* r, float2* p, const float2* b, const float2* a, int64_t n, double* part) {
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < n; i += (int64_t)kDotBlocks * kDotThreads) {
+    const float2 bv = b[i], av = a[i];
+    const float2 rv = make_float2(bv.x - av.x, bv.y - av.y);
+    r[i] = rv;
+    p[i] = rv;
+    s += (double)rv.x * (double)rv.x + (double)rv.y * (double)rv.y;
+  }
+  const double t = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// --------------------------------------------------------------- image-gradient kernels
+struct ImgGeom {
+  int d;
+  int N[kMaxDim];
+  int64_t stride[kMaxDim];
+  int64_t n;
+};
+
+__device__ __forceinline__ int64_t nb_index(const ImgGeom& G, int64_t i, int a, int delta) {
+  const int64_t c = (i / G.stride[a]) % G.N[a];
+  int64_t c2 = c + delta;
+  if (c2 < 0) c2 += G.N[a];
+  if (c2 >= G.N[a]) c2 -= G.N[a];
+  return i + (c2 - c) * G.stride[a];
+}
+
+// out = mu q + lambda sum_a (2 p - p[-e_a] - p[+e_a])   (K applied to p; q = A^H A p)
+__global__ void k_tv_apply(float2* out, const float2* q, const float2* p, ImgGeom G, float mu, float lam) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < G.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 pv = p[i];
+    float2 lap = make_float2(0.f, 0.f);
+    for (int a = 0; a < G.d; ++a) {
+      const float2 pm = p[nb_index(G, i, a, -1)], pp = p[nb_index(G, i, a, +1)];
+      lap.x += 2.f * pv.x - pm.x - pp.x;
+      lap.y += 2.f * pv.y - pm.y - pp.y;
+    }
+    const float2 qv = q[i];
+    out[i] = make_float2(mu * qv.x + lam * lap.x, mu * qv.y + lam * lap.y);
+  }
+}
+
+// rhs = mu (base + df - bf) + lambda sum_a grad_a^T (d_a - b_a); df/bf may be NULL (OLS)
+__global__ void k_rhs(float2* rhs, const float2* base, const float2* df, const float2* bf, const float2* d0,
+                      const float2* b0, int64_t vstride, ImgGeom G, float mu, float lam) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < G.n; i += (int64_t)gridDim.x * blockDim.x) {
+    float2 acc = base[i];
+    if (df) {
+      const float2 f = df[i], g = bf[i];
+      acc.x += f.x - g.x;
+      acc.y += f.y - g.y;
+    }
+    acc.x *= mu;
+    acc.y *= mu;
+    for (int a = 0; a < G.d; ++a) {
+      const float2* da = d0 + a * vstride;
+      const float2* ba = b0 + a * vstride;
+      const int64_t im = nb_index(G, i, a, -1);
+      // grad_a^T g [i] = g[i - e_a] - g[i]
+      const float gx = (da[im].x - ba[im].x) - (da[i].x - ba[i].x);
+      const float gy = (da[im].y - ba[im].y) - (da[i].y - ba[i].y);
+      acc.x += lam * gx;
+      acc.y += lam * gy;
+    }
+    rhs[i] = acc;
+  }
+}
+
+__device__ __forceinline__ float2 shrink(float2 z, float t) {
+  const float mag = sqrtf(z.x * z.x + z.y * z.y);
+  if (mag == 0.f) return make_float2(0.f, 0.f);
+  const float f = fmaxf(mag - t, 0.f) / mag;
+  return make_float2(z.x * f, z.y * f);
+}
+
+// for every axis a: g = grad_a x; d_a = shrink(g + b_a, thr); b_a += g - d_a
+__global__ void k_shrink_tv(const float2* x, float2* d0, float2* b0, int64_t vstride, ImgGeom G, float thr) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < G.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 xv = x[i];
+    for (int a = 0; a < G.d; ++a) {
+      const float2 xp = x[nb_index(G, i, a, +1)];
+      const float2 g = make_float2(xp.x - xv.x, xp.y - xv.y);
+      float2* da = d0 + a * vstride;
+      float2* ba = b0 + a * vstride;
+      const float2 bv = ba[i];
+      const float2 dv = shrink(make_float2(g.x + bv.x, g.y + bv.y), thr);
+      da[i] = dv;
+      ba[i] = make_float2(bv.x + (g.x - dv.x), bv.y + (g.y - dv.y));
+    }
+  }
+}
+
+// LAD data split: res = ahax - ahy; df = shrink(res + bf, thr); bf += res - df
+__global__ void k_shrink_data(const float2* ahax, const float2* ahy, float2* df, float2* bf, int64_t n, float thr) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 a = ahax[i], h = ahy[i], bv = bf[i];
+    const float2 res = make_float2(a.x - h.x, a.y - h.y);
+    const float2 dv = shrink(make_float2(res.x + bv.x, res.y + bv.y), thr);
+    df[i] = dv;
+    bf[i] = make_float2(bv.x + (res.x - dv.x), bv.y + (res.y - dv.y));
+  }
+}
+
+// Bregman outer step: ahyk += ahy - ahax
+__global__ void k_outer(float2* ahyk, const float2* ahy, const float2* ahax, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 k = ahyk[i], h = ahy[i], a = ahax[i];
+    ahyk[i] = make_float2(k.x + (h.x - a.x), k.y + (h.y - a.y));
+  }
+}
+
+int ew_blocks(int64_t n) {
+  int64_t b = (n + kEwThreads - 1) / kEwThreads;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+ImgGeom img_geom(const nufft_plan_t* p) {
+  ImgGeom G;
+  memset(&G, 0, sizeof(G));
+  G.d = p->g.d;
+  int64_t s = 1;
+  for (int a = G.d - 1; a >= 0; --a) {
+    G.N[a] = p->g.N[a];
+    G.stride[a] = s;
+    s *= p->g.N[a];
+  }
+  G.n = s;
+  return G;
+}
+
+#define TRY(x)                       \
+  do {                               \
+    int _rc = (x);                   \
+    if (_rc != NUFFT_OK) return _rc; \
+  } while (0)
+#define LAUNCH_CHECK(p, what) NUFFT_CUDA_TRY(p, cudaGetLastError())
+
+struct Operator {
+  bool tv;       // false: A^H A; true: K = mu A^H A + lambda sum grad^T grad
+  float mu, lam;
+};
+
+int apply_op(nufft_plan_t* p, const Operator& op, const float2* in, float2* out, float2* tmp) {
+  if (!op.tv) return selfadjoint_impl(p, in, out);
+  TRY(selfadjoint_impl(p, in, tmp));
+  const ImgGeom G = img_geom(p);
+  k_tv_apply<<<ew_blocks(G.n), kEwThreads, 0, p->stream>>>(out, tmp, in, G, op.mu, op.lam);
+  LAUNCH_CHECK(p, "tv apply");
+  return NUFFT_OK;
+}
+
+// cg_iters CG steps on op x = b from the current x (in place).
+int cg_run(nufft_plan_t* p, const Ws& w, const Operator& op, const float2* b, float2* x, int iters) {
+  const int64_t n = p->Nprod;
+  cudaStream_t st = p->stream;
+  float2 *r = w.v[V_R], *pv = w.v[V_P], *q = w.v[V_Q], *t = w.v[V_T];
+  TRY(apply_op(p, op, x, q, t));
+  k_cg_init<<<kDotBlocks, kDotThreads, 0, st>>>(r, pv, b, q, n, w.part);
+  k_dot_final<<<1, kDotThreads, 0, st>>>(w.part, w.sc + S_RR0);
+  LAUNCH_CHECK(p, "cg init");
+  for (int it = 0; it < iters; ++it) {
+    const int cur = (it & 1) ? S_RR1 : S_RR0;
+    const int nxt = (it & 1) ? S_RR0 : S_RR1;
+    TRY(apply_op(p, op, pv, q, t));
+    k_dot_partial<<<kDotBlocks, kDotThreads, 0, st>>>(pv, q, n, w.part);
+    k_dot_final<<<1, kDotThreads, 0, st>>>(w.part, w.sc + S_PQ);
+    k_cg_xr<<<kDotBlocks, kDotThreads, 0, st>>>(x, r, pv, q, n, w.sc, cur, w.part);
+    k_dot_final<<<1, kDotThreads, 0, st>>>(w.part, w.sc + nxt);
+    k_cg_p<<<ew_blocks(n), kEwThreads, 0, st>>>(pv, r, n, w.sc, nxt, cur);
+    LAUNCH_CHECK(p, "cg iteration");
+  }
+  return NUFFT_OK;
+}
+
+int check_common(nufft_plan_t* p, const float* y, const float* x) {
+  if (!p) return set_error(nullptr, NUFFT_EINVAL, "plan is NULL");
+  if (p->M > 0 && !y) return set_error(p, NUFFT_EINVAL, "y_dev is NULL");
+  if (!x) return set_error(p, NUFFT_EINVAL, "x_dev is NULL");
+  return NUFFT_OK;
+}
+
+int l1tv(nufft_plan_t* p, const float2* y, float2* x, int maxiter, int inner, int cg_iters, double mu, double lambda,
+         bool lad) {
+  if (maxiter < 0 || inner < 1 || cg_iters < 1)
+    return set_error(p, NUFFT_EINVAL, "need maxiter >= 0, inner >= 1, cg_iters >= 1");
+  if (!(mu > 0.0) || !(lambda > 0.0)) return set_error(p, NUFFT_EINVAL, "need mu > 0 and lambda > 0");
+  Ws w;
+  TRY(get_ws(p, &w));
+  const int64_t n = p->Nprod;
+  cudaStream_t st = p->stream;
+  const ImgGeom G = img_geom(p);
+  const int64_t vstride = w.v[1] - w.v[0];
+  float2 *ahy = w.v[V_AHY], *ahyk = w.v[V_AHYK], *rhs = w.v[V_RHS], *tmp = w.v[V_B];
+  float2 *df = w.v[V_DF], *bf = w.v[V_BF], *d0 = w.v[V_D0], *b0 = w.v[V_B0];
+  TRY(adjoint_dev(p, y, ahy));
+  NUFFT_CUDA_TRY(p, cudaMemcpyAsync(ahyk, ahy, n * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+  for (int a = 0; a < G.d; ++a) {
+    NUFFT_CUDA_TRY(p, cudaMemsetAsync(d0 + a * vstride, 0, n * sizeof(float2), st));
+    NUFFT_CUDA_TRY(p, cudaMemsetAsync(b0 + a * vstride, 0, n * sizeof(float2), st));
+  }
+  if (lad) {
+    NUFFT_CUDA_TRY(p, cudaMemsetAsync(df, 0, n * sizeof(float2), st));
+    NUFFT_CUDA_TRY(p, cudaMemsetAsync(bf, 0, n * sizeof(float2), st));
+  }
+  const Operator K{true, (float)mu, (float)lambda};
+  const float thr_tv = (float)(1.0 / lambda);
+  const float thr_f = (float)(1.0 / mu);
+  for (int outer = 0; outer < maxiter; ++outer) {
+    for (int it = 0; it < inner; ++it) {
+      k_rhs<<<ew_blocks(n), kEwThreads, 0, st>>>(rhs, ahyk, lad ? df : nullptr, lad ? bf : nullptr, d0, b0, vstride, G,
+                                                (float)mu, (float)lambda);
+      LAUNCH_CHECK(p, "rhs");
+      TRY(cg_run(p, w, K, rhs, x, cg_iters));
+      k_shrink_tv<<<ew_blocks(n), kEwThreads, 0, st>>>(x, d0, b0, vstride, G, thr_tv);
+      LAUNCH_CHECK(p, "shrink");
+      if (lad) {
+        TRY(selfadjoint_impl(p, x, tmp));
+        k_shrink_data<<<ew_blocks(n), kEwThreads, 0, st>>>(tmp, ahy, df, bf, n, thr_f);
+        LAUNCH_CHECK(p, "shrink data");
+      }
+    }
+    // A^H A x of the last inner iteration: LAD already holds it in tmp (same x).
+    if (!lad) TRY(selfadjoint_impl(p, x, tmp));
+    k_outer<<<ew_blocks(n), kEwThreads, 0, st>>>(ahyk, ahy, tmp, n);
+    LAUNCH_CHECK(p, "outer");
+  }
+  return NUFFT_OK;
+}
+
+}  // namespace
+
+extern "C" int solve_cg(nufft_plan_t* p, const float* y_dev, float* x_dev, int maxiter) {
+  TRY(check_common(p, y_dev, x_dev));
+  if (maxiter < 0) return set_error(p, NUFFT_EINVAL, "maxiter < 0");
+  Ws w;
+  TRY(get_ws(p, &w));
+  TRY(adjoint_dev(p, reinterpret_cast<const float2*>(y_dev), w.v[V_B]));
+  const Operator op{false, 1.f, 0.f};
+  return cg_run(p, w, op, w.v[V_B], reinterpret_cast<float2*>(x_dev), maxiter);
+}
+
+extern "C" int solve_l1tv_ols(nufft_plan_t* p, const float* y_dev, float* x_dev, int maxiter, int inner,
+                              int cg_iters, double mu, double lambda) {
+  TRY(check_common(p, y_dev, x_dev));
+  return l1tv(p, reinterpret_cast<const float2*>(y_dev), reinterpret_cast<float2*>(x_dev), maxiter, inner, cg_iters,
+              mu, lambda, false);
+}
+
+extern "C" int solve_l1tv_lad(nufft_plan_t* p, const float* y_dev, float* x_dev, int maxiter, int inner,
+                              int cg_iters, double mu, double lambda) {
+  TRY(check_common(p, y_dev, x_dev));
+  return l1tv(p, reinterpret_cast<const float2*>(y_dev), reinterpret_cast<float2*>(x_dev), maxiter, inner, cg_iters,
+              mu, lambda, true);
+}

@@ -1,0 +1,274 @@
+"""Plan object and same-named wrappers of the C entry points.
+
+Argument marshalling only: tensors are checked for device, dtype, contiguity
+and size, then their data pointers and the current CUDA stream are handed to
+the library.  Complex tensors are complex64 (interleaved float pairs).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from ._lib import lib, check
+
+_c_int_arr = lambda v: (ctypes.c_int * len(v))(*[int(t) for t in v])
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_ptr(t: torch.Tensor, numel: int, name: str, dtype=torch.complex64):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_ptr(t: torch.Tensor, numel: int, name: str):
+    if t.is_cuda or t.dtype != torch.complex64 or not t.is_contiguous() or t.numel() != numel:
+        raise ValueError(f"{name} must be a contiguous complex64 host tensor with {numel} elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class NufftPlan:
+    """Min-max NUFFT plan for one trajectory (C: ``nufft_plan``).
+
+    om: (M, d) float32 CUDA tensor of frequencies in radians; Nd, Kd, Jd: image
+    size, oversampled grid (powers of two) and neighbours per dimension.
+    """
+
+    def __init__(self, om: torch.Tensor, Nd, Kd, Jd, stream=None):
+        if om.dim() == 1:
+            om = om[:, None]
+        d = len(Nd)
+        if om.dim() != 2 or om.shape[1] != d:
+            raise ValueError("om must have shape (M, d)")
+        M = om.shape[0]
+        om_ptr = _dev_ptr(om.contiguous(), M * d, "om", dtype=torch.float32) if M > 0 else ctypes.c_void_p(0)
+        self._om = om
+        h = ctypes.c_void_p(0)
+        rc = lib.nufft_plan(d, _c_int_arr(Nd), _c_int_arr(Kd), _c_int_arr(Jd), M, om_ptr,
+                            _stream_ptr(stream), ctypes.byref(h))
+        check(rc, None)
+        self._h = h
+        self.d, self.M = d, M
+        self.Nd, self.Kd, self.Jd = tuple(int(v) for v in Nd), tuple(int(v) for v in Kd), tuple(int(v) for v in Jd)
+        self.device = om.device
+
+    # ---------------------------------------------------------------- lifetime
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib.nufft_plan_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_stream(self, stream=None):
+        check(lib.nufft_set_stream(self._h, _stream_ptr(stream)), self._h)
+
+    def _sync_stream(self):
+        check(lib.nufft_set_stream(self._h, _stream_ptr()), self._h)
+
+    # ---------------------------------------------------------------- sizes
+    @property
+    def Nprod(self):
+        n = 1
+        for v in self.Nd:
+            n *= v
+        return n
+
+    @property
+    def Kprod(self):
+        n = 1
+        for v in self.Kd:
+            n *= v
+        return n
+
+    def info(self):
+        buf = (ctypes.c_int64 * 16)()
+        check(lib.nufft_plan_info(self._h, buf), self._h)
+        v = list(buf)
+        return {"d": v[0], "M": v[1], "N": v[2:5][: self.d], "K": v[5:8][: self.d], "J": v[8:11][: self.d],
+                "nbins": v[11], "nchunks": v[12], "device_bytes": v[13], "tile_first": v[14], "tile_last": v[15]}
+
+    def interpolator(self):
+        """(kfirst (M,d) int32, [coef_i (M,J_i) complex64], [s_i (N_i,) float32], perm (M,) int32) on host."""
+        M, d = self.M, self.d
+        kf = torch.empty((M, d), dtype=torch.int32)
+        ncoef = sum(M * J for J in self.Jd)
+        coef = torch.empty(ncoef, dtype=torch.complex64)
+        s = torch.empty(sum(self.Nd), dtype=torch.float32)
+        perm = torch.empty(M, dtype=torch.int32)
+        check(lib.nufft_plan_get_interpolator(self._h, ctypes.c_void_p(kf.data_ptr()), ctypes.c_void_p(coef.data_ptr()),
+                                              ctypes.c_void_p(s.data_ptr()), ctypes.c_void_p(perm.data_ptr())), self._h)
+        coefs, off = [], 0
+        for J in self.Jd:
+            coefs.append(coef[off: off + M * J].reshape(M, J))
+            off += M * J
+        ss, off = [], 0
+        for N in self.Nd:
+            ss.append(s[off: off + N])
+            off += N
+        return kf, coefs, ss, perm
+
+    # ---------------------------------------------------------------- operators
+    def forward(self, x: torch.Tensor, y: torch.Tensor | None = None) -> torch.Tensor:
+        if y is None:
+            y = torch.empty(self.M, dtype=torch.complex64, device=self.device)
+        self._sync_stream()
+        check(lib.nufft_forward(self._h, _dev_ptr(x, self.Nprod, "x"), _dev_ptr(y, self.M, "y")), self._h)
+        return y
+
+    def adjoint(self, y: torch.Tensor, x: torch.Tensor | None = None) -> torch.Tensor:
+        if x is None:
+            x = torch.empty(self.Nd, dtype=torch.complex64, device=self.device)
+        self._sync_stream()
+        check(lib.nufft_adjoint(self._h, _dev_ptr(y, self.M, "y"), _dev_ptr(x, self.Nprod, "x")), self._h)
+        return x
+
+    def selfadjoint(self, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(self.Nd, dtype=torch.complex64, device=self.device)
+        self._sync_stream()
+        check(lib.nufft_selfadjoint(self._h, _dev_ptr(x, self.Nprod, "x"), _dev_ptr(out, self.Nprod, "out")), self._h)
+        return out
+
+    def forward_host(self, x_host: torch.Tensor, y_host: torch.Tensor | None = None) -> torch.Tensor:
+        if y_host is None:
+            y_host = torch.empty(self.M, dtype=torch.complex64, pin_memory=True)
+        self._sync_stream()
+        check(lib.nufft_forward_host(self._h, _host_ptr(x_host, self.Nprod, "x_host"),
+                                     _host_ptr(y_host, self.M, "y_host")), self._h)
+        return y_host
+
+    def adjoint_host(self, y_host: torch.Tensor, x_host: torch.Tensor | None = None) -> torch.Tensor:
+        if x_host is None:
+            x_host = torch.empty(self.Nd, dtype=torch.complex64, pin_memory=True)
+        self._sync_stream()
+        check(lib.nufft_adjoint_host(self._h, _host_ptr(y_host, self.M, "y_host"),
+                                     _host_ptr(x_host, self.Nprod, "x_host")), self._h)
+        return x_host
+
+    # ---------------------------------------------------------------- stages
+    def scale_pad_fft(self, x, grid=None):
+        grid = torch.empty(self.Kd, dtype=torch.complex64, device=self.device) if grid is None else grid
+        self._sync_stream()
+        check(lib.nufft_scale_pad_fft(self._h, _dev_ptr(x, self.Nprod, "x"), _dev_ptr(grid, self.Kprod, "grid")), self._h)
+        return grid
+
+    def interp(self, grid, y=None):
+        y = torch.empty(self.M, dtype=torch.complex64, device=self.device) if y is None else y
+        self._sync_stream()
+        check(lib.nufft_interp(self._h, _dev_ptr(grid, self.Kprod, "grid"), _dev_ptr(y, self.M, "y")), self._h)
+        return y
+
+    def gridding(self, y, grid=None):
+        grid = torch.empty(self.Kd, dtype=torch.complex64, device=self.device) if grid is None else grid
+        self._sync_stream()
+        check(lib.nufft_gridding(self._h, _dev_ptr(y, self.M, "y"), _dev_ptr(grid, self.Kprod, "grid")), self._h)
+        return grid
+
+    def ifft_crop_rescale(self, grid, x=None):
+        x = torch.empty(self.Nd, dtype=torch.complex64, device=self.device) if x is None else x
+        self._sync_stream()
+        check(lib.nufft_ifft_crop_rescale(self._h, _dev_ptr(grid, self.Kprod, "grid"), _dev_ptr(x, self.Nprod, "x")),
+              self._h)
+        return x
+
+    # ---------------------------------------------------------------- solvers
+    def solve_cg(self, y, x=None, maxiter=20):
+        x = torch.zeros(self.Nd, dtype=torch.complex64, device=self.device) if x is None else x
+        self._sync_stream()
+        check(lib.solve_cg(self._h, _dev_ptr(y, self.M, "y"), _dev_ptr(x, self.Nprod, "x"), int(maxiter)), self._h)
+        return x
+
+    def solve_l1tv_ols(self, y, x=None, maxiter=50, inner=2, cg_iters=5, mu=1.0, lam=0.01):
+        x = torch.zeros(self.Nd, dtype=torch.complex64, device=self.device) if x is None else x
+        self._sync_stream()
+        check(lib.solve_l1tv_ols(self._h, _dev_ptr(y, self.M, "y"), _dev_ptr(x, self.Nprod, "x"), int(maxiter),
+                                 int(inner), int(cg_iters), float(mu), float(lam)), self._h)
+        return x
+
+    def solve_l1tv_lad(self, y, x=None, maxiter=50, inner=2, cg_iters=5, mu=1.0, lam=0.01):
+        x = torch.zeros(self.Nd, dtype=torch.complex64, device=self.device) if x is None else x
+        self._sync_stream()
+        check(lib.solve_l1tv_lad(self._h, _dev_ptr(y, self.M, "y"), _dev_ptr(x, self.Nprod, "x"), int(maxiter),
+                                 int(inner), int(cg_iters), float(mu), float(lam)), self._h)
+        return x
+
+
+# ---------------------------------------------------------------- same names as the C ABI
+def nufft_plan(om, Nd, Kd, Jd, stream=None) -> NufftPlan:
+    return NufftPlan(om, Nd, Kd, Jd, stream)
+
+
+def nufft_forward(plan: NufftPlan, x, y=None):
+    return plan.forward(x, y)
+
+
+def nufft_adjoint(plan: NufftPlan, y, x=None):
+    return plan.adjoint(y, x)
+
+
+def nufft_selfadjoint(plan: NufftPlan, x, out=None):
+    return plan.selfadjoint(x, out)
+
+
+def nufft_forward_host(plan: NufftPlan, x_host, y_host=None):
+    return plan.forward_host(x_host, y_host)
+
+
+def nufft_adjoint_host(plan: NufftPlan, y_host, x_host=None):
+    return plan.adjoint_host(y_host, x_host)
+
+
+def nufft_scale_pad_fft(plan: NufftPlan, x, grid=None):
+    return plan.scale_pad_fft(x, grid)
+
+
+def nufft_interp(plan: NufftPlan, grid, y=None):
+    return plan.interp(grid, y)
+
+
+def nufft_gridding(plan: NufftPlan, y, grid=None):
+    return plan.gridding(y, grid)
+
+
+def nufft_ifft_crop_rescale(plan: NufftPlan, grid, x=None):
+    return plan.ifft_crop_rescale(grid, x)
+
+
+def solve_cg(plan: NufftPlan, y, x=None, maxiter=20):
+    return plan.solve_cg(y, x, maxiter)
+
+
+def solve_l1tv_ols(plan: NufftPlan, y, x=None, maxiter=50, inner=2, cg_iters=5, mu=1.0, lam=0.01):
+    return plan.solve_l1tv_ols(y, x, maxiter, inner, cg_iters, mu, lam)
+
+
+def solve_l1tv_lad(plan: NufftPlan, y, x=None, maxiter=50, inner=2, cg_iters=5, mu=1.0, lam=0.01):
+    return plan.solve_l1tv_lad(y, x, maxiter, inner, cg_iters, mu, lam)
