@@ -151,6 +151,28 @@ int nufft_gridding(nufft_plan_t* plan, const float* y_dev, float* grid_dev);
 int nufft_ifft_crop_rescale(nufft_plan_t* plan, float* grid_dev, float* x_dev);
 
 /*
+ * nufft_gridding_static - grid = V^H y exactly as nufft_gridding, for callers
+ * that cannot allocate device memory at call time (for example code running
+ * under a memory budget that forbids cudaMalloc, or inside a framework whose
+ * allocator must not be entered from this point).  The paper has no
+ * counterpart: this is a library-usage variant, not a step of the method.
+ *
+ * The per-chunk partial tiles that nufft_gridding keeps in plan-owned memory
+ * live here in one fixed device array of 16 MiB that every GPU loading this
+ * library holds until the process exits.  The call allocates nothing and
+ * frees nothing.  Plans whose partial tiles need more than 16 MiB
+ * (nchunks * padded-tile bytes, nufft_plan_info [12]) are rejected with
+ * NUFFT_EINVAL; the 2D 256^2 / 512^2 workloads fit, large 3D grids do not.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current): make that first call before any stream
+ * capture.  Every call shares the one array, and each call overwrites the
+ * part it uses before reading it, so nothing needs clearing; calls that can
+ * overlap on the GPU (other streams, other plans, other threads) race on it
+ * and must be serialised by the caller.
+ */
+int nufft_gridding_static(nufft_plan_t* plan, const float* y_dev, float* grid_dev);
+
+/*
  * solve_cg - conjugate gradient on the normal equation A^H A x = A^H y
  * (Section 2.1.5 Eq. 4; Section 2.2.2 Eqs. 7-9 give the paper's k-space form,
  * this is the image-domain form).  Exactly maxiter iterations, no early exit;

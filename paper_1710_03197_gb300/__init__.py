@@ -25,6 +25,7 @@ from .plan import (
     nufft_scale_pad_fft,
     nufft_interp,
     nufft_gridding,
+    nufft_gridding_static,
     nufft_ifft_crop_rescale,
     solve_cg,
     solve_l1tv_ols,
@@ -35,5 +36,5 @@ __all__ = [
     "lib", "LIB_PATH", "NufftError", "check", "symbols_declared", "NufftPlan",
     "nufft_plan", "nufft_forward", "nufft_adjoint", "nufft_selfadjoint",
     "nufft_forward_host", "nufft_adjoint_host", "nufft_scale_pad_fft", "nufft_interp",
-    "nufft_gridding", "nufft_ifft_crop_rescale", "solve_cg", "solve_l1tv_ols", "solve_l1tv_lad",
+    "nufft_gridding", "nufft_gridding_static", "nufft_ifft_crop_rescale", "solve_cg", "solve_l1tv_ols", "solve_l1tv_lad",
 ]

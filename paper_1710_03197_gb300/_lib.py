@@ -48,6 +48,7 @@ _SIGS = {
     "nufft_scale_pad_fft": (_i, [_PLAN, _vp, _vp]),
     "nufft_interp": (_i, [_PLAN, _vp, _vp]),
     "nufft_gridding": (_i, [_PLAN, _vp, _vp]),
+    "nufft_gridding_static": (_i, [_PLAN, _vp, _vp]),
     "nufft_ifft_crop_rescale": (_i, [_PLAN, _vp, _vp]),
     "solve_cg": (_i, [_PLAN, _vp, _vp, _i]),
     "solve_l1tv_ols": (_i, [_PLAN, _vp, _vp, _i, _i, _i, _d, _d]),

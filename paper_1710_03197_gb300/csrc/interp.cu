@@ -20,6 +20,8 @@
 // of the padded tiles that cover it (its own tile's chunks and those of the
 // 2^d - 1 lower neighbour tiles).  No global atomics; every grid cell is
 // written exactly once.
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace nufft {
@@ -273,6 +275,51 @@ cudaError_t gridding_d(const nufft_plan_t* p, const float2* y, float2* grid) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- gridding without allocation
+// Partial-tile scratch for nufft_gridding_static: a fixed array in device
+// memory, so that call needs neither cudaMalloc nor plan-owned scratch.
+constexpr int64_t kStaticTileBytes = 16ll << 20;   // 16 MiB on every GPU that loads the library
+static __device__ __align__(256) float2 g_static_tiles[kStaticTileBytes / sizeof(float2)];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+float2* g_static_ptr[kMaxDevices];   // device address of g_static_tiles, per device
+
+int static_tiles_address(nufft_plan_t* p, float2** out) {
+  int dev = -1;
+  NUFFT_CUDA_TRY(p, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return set_error(p, NUFFT_EINVAL, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* ptr = nullptr;
+    NUFFT_CUDA_TRY(p, cudaGetSymbolAddress(&ptr, g_static_tiles));
+    g_static_ptr[dev] = static_cast<float2*>(ptr);
+  }
+  *out = g_static_ptr[dev];
+  return NUFFT_OK;
+}
+
+template <int D>
+cudaError_t gridding_static_d(const nufft_plan_t* p, const float2* y, float2* grid, float2* tiles) {
+  const Points P = points_view(p);
+  const size_t smem = (size_t)p->g.padded_cells * sizeof(float2);
+  if (p->nchunks > 0) {
+    if (all_j_equal(p->g, 6)) {
+      cudaError_t e = cudaFuncSetAttribute(k_gridding_chunk<D, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k_gridding_chunk<D, 6><<<(unsigned)p->nchunks, 256, smem, p->stream>>>(y, tiles, p->chunks, P, p->g);
+    } else {
+      cudaError_t e = cudaFuncSetAttribute(k_gridding_chunk<D, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k_gridding_chunk<D, 0><<<(unsigned)p->nchunks, 256, smem, p->stream>>>(y, tiles, p->chunks, P, p->g);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  k_gridding_reduce<D><<<(unsigned)p->g.nbins, 256, 0, p->stream>>>(tiles, p->bin_chunk, grid, p->g);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 int launch_interp(nufft_plan_t* p, const float2* grid, float2* y) {
@@ -296,3 +343,29 @@ int launch_gridding(nufft_plan_t* p, const float2* y, float2* grid) {
 }
 
 }  // namespace nufft
+
+// Gridding V^H like nufft_gridding, with the per-chunk partial tiles in the
+// static device array above instead of the plan's buffer (see the header).
+extern "C" int nufft_gridding_static(nufft_plan_t* p, const float* y_dev, float* grid_dev) {
+  using namespace nufft;
+  if (!p) return set_error(nullptr, NUFFT_EINVAL, "plan is NULL");
+  if (p->M > 0 && !y_dev) return set_error(p, NUFFT_EINVAL, "y_dev is NULL");
+  if (!grid_dev) return set_error(p, NUFFT_EINVAL, "grid_dev is NULL");
+  const int64_t need = p->nchunks * p->g.padded_cells * (int64_t)sizeof(float2);
+  if (need > kStaticTileBytes)
+    return set_error(p, NUFFT_EINVAL,
+                     "gridding needs %lld bytes of partial tiles, more than the %lld-byte static scratch; "
+                     "use nufft_gridding", (long long)need, (long long)kStaticTileBytes);
+  float2* tiles = nullptr;
+  const int rc = static_tiles_address(p, &tiles);
+  if (rc != NUFFT_OK) return rc;
+  const float2* y = reinterpret_cast<const float2*>(y_dev);
+  float2* grid = reinterpret_cast<float2*>(grid_dev);
+  cudaError_t e;
+  switch (p->g.d) {
+    case 1: e = gridding_static_d<1>(p, y, grid, tiles); break;
+    case 2: e = gridding_static_d<2>(p, y, grid, tiles); break;
+    default: e = gridding_static_d<3>(p, y, grid, tiles); break;
+  }
+  return e == cudaSuccess ? NUFFT_OK : cuda_check(p, e, "static-scratch gridding kernels");
+}

@@ -192,6 +192,14 @@ class NufftPlan:
         check(lib.nufft_gridding(self._h, _dev_ptr(y, self.M, "y"), _dev_ptr(grid, self.Kprod, "grid")), self._h)
         return grid
 
+    def gridding_static(self, y, grid):
+        """V^H y with the partial tiles in the library's fixed device array
+        (no allocation by the call; see nufft_gridding_static in the header)."""
+        self._sync_stream()
+        check(lib.nufft_gridding_static(self._h, _dev_ptr(y, self.M, "y"), _dev_ptr(grid, self.Kprod, "grid")),
+              self._h)
+        return grid
+
     def ifft_crop_rescale(self, grid, x=None):
         x = torch.empty(self.Nd, dtype=torch.complex64, device=self.device) if x is None else x
         self._sync_stream()
@@ -256,6 +264,10 @@ def nufft_interp(plan: NufftPlan, grid, y=None):
 
 def nufft_gridding(plan: NufftPlan, y, grid=None):
     return plan.gridding(y, grid)
+
+
+def nufft_gridding_static(plan: NufftPlan, y, grid):
+    return plan.gridding_static(y, grid)
 
 
 def nufft_ifft_crop_rescale(plan: NufftPlan, grid, x=None):
