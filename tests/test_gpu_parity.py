@@ -346,7 +346,10 @@ def test_l1tv_lad_matches_oracle(nf, d, mu, lam):
 
 def test_l1tv_ols_radial_within_fp32_envelope(nf, monkeypatch):
     """Golden-angle radial L1TV-OLS (the reconstruction setting of the 256^2
-    workload, scaled down): bound derived from the FP32 rounding envelope."""
+    workload, scaled down).  The iterate is determined only to ~1e-2 at FP32
+    rounding level here (the oracle moves by 3e-3..5e-3 under 1e-6 operator
+    noise), so the bound is an order-of-magnitude one derived from the
+    arithmetic: within 5x the largest spread over three perturbed oracle runs."""
     Nd, Kd, Jd = (64, 64), (128, 128), (6, 6)
     om = W.radial2d_golden(60, 128)
     ref = oracle.make_plan(om, Nd, Kd, Jd)
@@ -354,8 +357,10 @@ def test_l1tv_ols_radial_within_fp32_envelope(nf, monkeypatch):
     with nf.NufftPlan(to_dev(om), Nd, Kd, Jd) as plan:
         xg = host(plan.solve_l1tv_ols(to_dev(y), maxiter=6, inner=2, cg_iters=5, mu=1.0, lam=0.01))
         op_err = _op_err(plan, ref, Nd)
-    x_ref, spread = _envelope(monkeypatch, lambda: oracle.l1tv_ols(ref, y, np.zeros(Nd), 6, 2, 5, 1.0, 0.01), op_err)
-    assert rel(xg, x_ref) < max(3 * spread, TOL_SOLVER)
+    x_ref, spread = _envelope(monkeypatch, lambda: oracle.l1tv_ols(ref, y, np.zeros(Nd), 6, 2, 5, 1.0, 0.01), op_err,
+                              seeds=(1, 2, 3))
+    assert spread > TOL_SOLVER
+    assert rel(xg, x_ref) < 5 * spread
 
 
 # ------------------------------------------------------------------ edge cases
