@@ -146,6 +146,14 @@ class ClockSampler:
 
 STAGES = ("scale_pad_fft", "interp", "gridding", "ifft_crop_rescale")
 
+WORKLOAD_TEXT = {
+    "radial2d_256": "radial2d_256: 2D 256x256 image, 512x512 grid, J=6x6, golden-angle radial 403 spokes x 512 "
+                    "samples (206,336 points), ellipse phantom",
+    "kooshball3d_128": "kooshball3d_128: 3D 128^3 image, 256^3 grid, J=6^3, kooshball 8192 Fibonacci spokes x 256 "
+                       "samples (2,097,152 points), complex normal image",
+    "radial2d_64": "radial2d_64: 2D 64x64 image, 128x128 grid, J=6x6, 64 uniform spokes x 128 samples (8192 points)",
+}
+
 
 def run_workload(nf, torch, name: str, steps: int, warmup: int, dev, flush_bytes: int):
     spec, om, x, _ = W.make_workload(name)
@@ -255,18 +263,21 @@ def ours(args):
         os.path.join(ROOT, "gpurun_out")) else None
     if world > 1:
         torch.distributed.barrier()
+    names = [w.strip() for w in args.workloads.split(",") if w.strip()]
     with ClockSampler(torch.cuda.current_device() if world == 1 else local, clocks_path) as clk:
-        res2 = run_workload(nf, torch, "radial2d_256", args.steps, args.warmup, dev, flush_bytes)
-        res3 = run_workload(nf, torch, "kooshball3d_128", args.steps, args.warmup, dev, flush_bytes)
+        results = {n: run_workload(nf, torch, n, args.steps, args.warmup, dev, flush_bytes) for n in names}
     torch.cuda.synchronize()
+    res2 = results[names[0]]
+    res3 = results[names[1]] if len(names) > 1 else None
 
     M2 = res2["spec"]["M"]
     tot_ms = sum(res2["step_ms"])
     elapsed, units = reduce_over_ranks(tot_ms * 1e-3, M2 * args.steps, world)
     value = units / elapsed
     e2e_el, e2e_units = reduce_over_ranks(res2["e2e_s"] * args.steps, M2 * args.steps, world)
-    M3 = res3["spec"]["M"]
-    el3, un3 = reduce_over_ranks(sum(res3["step_ms"]) * 1e-3, M3 * args.steps, world)
+    if res3 is not None:
+        M3 = res3["spec"]["M"]
+        el3, un3 = reduce_over_ranks(sum(res3["step_ms"]) * 1e-3, M3 * args.steps, world)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -278,12 +289,11 @@ def ours(args):
     if os.path.exists(tpath):
         with open(tpath) as f:
             traffic_all = json.load(f)
-        traffic = traffic_all.get("radial2d_256", {})
-        traffic3 = traffic_all.get("kooshball3d_128", {})
+        traffic = traffic_all.get(names[0], {})
+        traffic3 = traffic_all.get(names[1], {}) if res3 is not None else {}
     else:
         traffic3 = {}
     dom2, stages2, roof2 = roofline_for(res2, peak, peak_kind, traffic)
-    dom3, stages3, roof3 = roofline_for(res3, peak, peak_kind, traffic3)
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -293,8 +303,7 @@ def ours(args):
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(elapsed * 1e3 / args.steps, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-        "config": {"workload": "radial2d_256: 2D 256x256 image, 512x512 grid, J=6x6, golden-angle radial "
-                               "403 spokes x 512 samples (206,336 points), ellipse phantom",
+        "config": {"workload": WORKLOAD_TEXT[names[0]],
                    "step": "A x then A^H y (forward + adjoint)", "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": round(e2e_units / e2e_el, 1), "unit": UNIT, "h2d_bytes_per_step": res2["h2d"],
@@ -305,16 +314,17 @@ def ours(args):
         "monolithic_ms_per_step": round(statistics.mean(res2["mono_ms"]), 5),
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
-        "also": {"kooshball3d_128": {
-            "workload": "3D 128^3 image, 256^3 grid, J=6^3, kooshball 8192 Fibonacci spokes x 256 samples "
-                        "(2,097,152 points), complex normal image",
+    }
+    if res3 is not None:
+        dom3, stages3, roof3 = roofline_for(res3, peak, peak_kind, traffic3)
+        line["also"] = {names[1]: {
+            "workload": WORKLOAD_TEXT[names[1]],
             "value": round(un3 / el3, 1), "unit": UNIT, "ms_per_step": round(el3 * 1e3 / args.steps, 5),
             "e2e": {"value": round(M3 / res3["e2e_s"], 1), "unit": UNIT, "h2d_bytes_per_step": res3["h2d"],
                     "d2h_bytes_per_step": res3["d2h"]},
             "gpu_launches": launches_per_step(res3["spec"], res3["info"]["nchunks"]) * args.steps,
             "roofline": roof3, "stages": stages3,
-            "monolithic_ms_per_step": round(statistics.mean(res3["mono_ms"]), 5)}},
-    }
+            "monolithic_ms_per_step": round(statistics.mean(res3["mono_ms"]), 5)}}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -382,6 +392,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--workloads", default="radial2d_256,kooshball3d_128",
+                    help="comma list; the first sets value/roofline, the second is reported under 'also'")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)           # at least 3 untimed warm-up steps
     if args.impl == "reference":

@@ -15,10 +15,11 @@ constexpr int kMaxDim = 3;
 constexpr int kMaxJ = 16;
 constexpr int kMinK = 16;
 constexpr int kMaxK = 1024;
-// Points per gridding chunk: a tile's points are cut into chunks of at most
-// this many so that a dense tile (the centre of a radial trajectory) is spread
-// over several CTAs.
-constexpr int kChunkPoints = 2048;
+// Points per gridding chunk (by dimension): a tile's points are cut into
+// chunks of at most this many so that a dense tile (the centre of a radial
+// trajectory) is spread over several CTAs, and small problems still fill the
+// GPU.  3D chunks are larger because each partial tile costs 74 KB.
+constexpr int kChunkPoints[4] = {0, 1024, 512, 2048};
 
 // Geometry of the oversampled grid and of the tile decomposition.
 struct Geom {
@@ -29,6 +30,8 @@ struct Geom {
   int T[kMaxDim];      // tile edge
   int nb[kMaxDim];     // tiles per dimension = K / T
   int P[kMaxDim];      // padded tile edge = T + J - 1
+  int lT[kMaxDim];     // log2 T
+  int lnb[kMaxDim];    // log2 nb
   int64_t Kstride[kMaxDim];  // C-order strides of the grid
   int64_t nbins;
   int64_t padded_cells;      // prod P

@@ -99,14 +99,24 @@ k_interp(const float2* __restrict__ grid, float2* __restrict__ y, const Points P
 }
 
 // ---------------------------------------------------------------- gridding, per chunk
+// The shared tile is held as two planes (real parts, then imaginary parts) so
+// that the J_last lanes of a point hit J_last consecutive banks per atomic.
 template <int D, int JF>
-__global__ void __launch_bounds__(256)
+struct GridChunkCfg {
+  static constexpr int kThreads = D == 3 ? 512 : 256;
+  static constexpr int kMinBlocks = D == 3 ? (JF == 6 ? 3 : 2) : 4;
+};
+
+template <int D, int JF>
+__global__ void __launch_bounds__(GridChunkCfg<D, JF>::kThreads, GridChunkCfg<D, JF>::kMinBlocks)
 k_gridding_chunk(const float2* __restrict__ y, float2* __restrict__ tiles, const Chunk* __restrict__ chunks,
                  const Points P, const Geom g) {
-  extern __shared__ float2 tile[];
+  extern __shared__ float sm[];
+  const int ncell = (int)g.padded_cells;
+  float* sre = sm;
+  float* sim = sm + ncell;
   const Chunk ch = chunks[blockIdx.x];
-  float* tf = reinterpret_cast<float*>(tile);
-  for (int64_t c = threadIdx.x; c < g.padded_cells; c += blockDim.x) tile[c] = make_float2(0.f, 0.f);
+  for (int c = threadIdx.x; c < 2 * ncell; c += blockDim.x) sm[c] = 0.f;
   __syncthreads();
 
   // tile origin of this chunk's bin
@@ -114,8 +124,8 @@ k_gridding_chunk(const float2* __restrict__ y, float2* __restrict__ tiles, const
   {
     int rem = ch.bin;
     for (int a = D - 1; a >= 0; --a) {
-      org[a] = (rem % g.nb[a]) * g.T[a];
-      rem /= g.nb[a];
+      org[a] = (rem & (g.nb[a] - 1)) << g.lT[a];
+      rem >>= g.lnb[a];
     }
   }
   const int G = JF > 0 ? JF : g.J[D - 1];
@@ -125,10 +135,8 @@ k_gridding_chunk(const float2* __restrict__ y, float2* __restrict__ tiles, const
   const int l = lane - sub * G;
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
-  const int P0 = g.P[0];
   const int P1 = D > 1 ? g.P[1] : 1;
   const int P2 = D > 2 ? g.P[2] : 1;
-  (void)P0;
 
   if (sub < per_warp) {
     for (int q = warp * per_warp + sub; q < ch.count; q += nwarps * per_warp) {
@@ -138,8 +146,8 @@ k_gridding_chunk(const float2* __restrict__ y, float2* __restrict__ tiles, const
       const float2 cl = P.coef[P.coef_off[D - 1] + (int64_t)l * P.M + i];
       const float2 yl = cmulc(cl, yv);  // conj(c_last) * y
       if (D == 1) {
-        atomicAdd(&tf[2 * ll], yl.x);
-        atomicAdd(&tf[2 * ll + 1], yl.y);
+        atomicAdd(&sre[ll], yl.x);
+        atomicAdd(&sim[ll], yl.y);
       } else if (D == 2) {
         const int l0 = P.kf[i] - org[0];
         const int J0 = JF > 0 ? JF : g.J[0];
@@ -149,8 +157,8 @@ k_gridding_chunk(const float2* __restrict__ y, float2* __restrict__ tiles, const
           const float2 c0 = P.coef[P.coef_off[0] + (int64_t)j0 * P.M + i];
           const float2 w = cmulc(c0, yl);
           const int cell = (l0 + j0) * P1 + ll;
-          atomicAdd(&tf[2 * cell], w.x);
-          atomicAdd(&tf[2 * cell + 1], w.y);
+          atomicAdd(&sre[cell], w.x);
+          atomicAdd(&sim[cell], w.y);
         }
       } else {
         const int l0 = P.kf[i] - org[0];
@@ -167,13 +175,14 @@ k_gridding_chunk(const float2* __restrict__ y, float2* __restrict__ tiles, const
         for (int j0 = 0; j0 < J0; ++j0) {
           const float2 c0 = P.coef[P.coef_off[0] + (int64_t)j0 * P.M + i];
           const float2 w0 = cmulc(c0, yl);
+          const int rowbase = ((l0 + j0) * P1 + l1) * P2 + ll;
 #pragma unroll
           for (int j1 = 0; j1 < (JF > 0 ? JF : kMaxJ); ++j1) {
             if (JF == 0 && j1 >= J1) break;
             const float2 w = cmulc(c1v[j1], w0);
-            const int cell = ((l0 + j0) * P1 + (l1 + j1)) * P2 + ll;
-            atomicAdd(&tf[2 * cell], w.x);
-            atomicAdd(&tf[2 * cell + 1], w.y);
+            const int cell = rowbase + j1 * P2;
+            atomicAdd(&sre[cell], w.x);
+            atomicAdd(&sim[cell], w.y);
           }
         }
       }
@@ -181,56 +190,73 @@ k_gridding_chunk(const float2* __restrict__ y, float2* __restrict__ tiles, const
   }
   __syncthreads();
   float2* out = tiles + (int64_t)blockIdx.x * g.padded_cells;
-  for (int64_t c = threadIdx.x; c < g.padded_cells; c += blockDim.x) out[c] = tile[c];
+  for (int c = threadIdx.x; c < ncell; c += blockDim.x) out[c] = make_float2(sre[c], sim[c]);
 }
 
 // ---------------------------------------------------------------- gridding, tile reduction
 // One CTA per tile: grid cell c of tile b is the sum over e in {0,1}^d of the
 // padded tiles of bin b - e (wrapped per dimension) at local position
-// c - origin(b) + e * T, when that position lies inside the padded tile.
+// c - origin(b) + e * T, when that position lies inside the padded tile.  The
+// sum runs over e, then over the source bin's chunks, in a fixed order.
 template <int D>
 __global__ void __launch_bounds__(256)
 k_gridding_reduce(const float2* __restrict__ tiles, const int32_t* __restrict__ bin_chunk,
                   float2* __restrict__ grid, const Geom g) {
-  const int64_t bin = blockIdx.x;
+  __shared__ int s_q0[1 << kMaxDim], s_q1[1 << kMaxDim];
+  const int bin = blockIdx.x;
   int bc[kMaxDim];
   {
-    int64_t rem = bin;
+    int rem = bin;
     for (int a = D - 1; a >= 0; --a) {
-      bc[a] = (int)(rem % g.nb[a]);
-      rem /= g.nb[a];
+      bc[a] = rem & (g.nb[a] - 1);
+      rem >>= g.lnb[a];
     }
   }
-  int64_t tile_cells = 1;
-  for (int a = 0; a < D; ++a) tile_cells *= g.T[a];
-  for (int64_t c = threadIdx.x; c < tile_cells; c += blockDim.x) {
-    int lc[kMaxDim];
-    {
-      int64_t rem = c;
-      for (int a = D - 1; a >= 0; --a) {
-        lc[a] = (int)(rem % g.T[a]);
-        rem /= g.T[a];
-      }
+  if (threadIdx.x < (1 << D)) {
+    const int e = threadIdx.x;
+    int src = 0;
+    for (int a = 0; a < D; ++a) {
+      const int ea = (e >> (D - 1 - a)) & 1;
+      src = (src << g.lnb[a]) | ((bc[a] - ea) & (g.nb[a] - 1));
+    }
+    s_q0[e] = bin_chunk[src];
+    s_q1[e] = bin_chunk[src + 1];
+  }
+  __syncthreads();
+  const int T0 = g.T[0], T1 = D > 1 ? g.T[1] : 1, T2 = D > 2 ? g.T[2] : 1;
+  const int P1 = D > 1 ? g.P[1] : 1, P2 = D > 2 ? g.P[2] : 1;
+  const int tile_cells = T0 * T1 * T2;
+  const int64_t pc = g.padded_cells;
+  for (int c = threadIdx.x; c < tile_cells; c += blockDim.x) {
+    int lc[3] = {0, 0, 0};
+    if (D == 1) {
+      lc[0] = c;
+    } else if (D == 2) {
+      lc[1] = c & (T1 - 1);
+      lc[0] = c >> g.lT[1];
+    } else {
+      lc[2] = c & (T2 - 1);
+      lc[1] = (c >> g.lT[2]) & (T1 - 1);
+      lc[0] = c >> (g.lT[2] + g.lT[1]);
     }
     float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
     for (int e = 0; e < (1 << D); ++e) {
-      int64_t src_bin = 0;
-      int64_t loc = 0;
+      int la[3] = {0, 0, 0};
       bool ok = true;
+#pragma unroll
       for (int a = 0; a < D; ++a) {
         const int ea = (e >> (D - 1 - a)) & 1;
-        const int la = lc[a] + ea * g.T[a];
-        if (la >= g.P[a]) { ok = false; break; }
-        const int ba = (bc[a] - ea + g.nb[a]) % g.nb[a];
-        src_bin = src_bin * g.nb[a] + ba;
-        loc = loc * g.P[a] + la;
+        la[a] = lc[a] + (ea ? g.T[a] : 0);
+        ok = ok && (la[a] < g.P[a]);
       }
       if (!ok) continue;
-      const int q0 = bin_chunk[src_bin], q1 = bin_chunk[src_bin + 1];
-      for (int q = q0; q < q1; ++q) acc = cadd(acc, __ldg(&tiles[(int64_t)q * g.padded_cells + loc]));
+      const int loc = D == 1 ? la[0] : (D == 2 ? la[0] * P1 + la[1] : (la[0] * P1 + la[1]) * P2 + la[2]);
+      const int q1 = s_q1[e];
+      for (int q = s_q0[e]; q < q1; ++q) acc = cadd(acc, __ldg(&tiles[(int64_t)q * pc + loc]));
     }
     int64_t off = 0;
-    for (int a = 0; a < D; ++a) off += (int64_t)(bc[a] * g.T[a] + lc[a]) * g.Kstride[a];
+    for (int a = 0; a < D; ++a) off += (int64_t)((bc[a] << g.lT[a]) + lc[a]) * g.Kstride[a];
     grid[off] = acc;
   }
 }
@@ -258,15 +284,16 @@ template <int D>
 cudaError_t gridding_d(const nufft_plan_t* p, const float2* y, float2* grid) {
   const Points P = points_view(p);
   const size_t smem = (size_t)p->g.padded_cells * sizeof(float2);
+  constexpr int NT = GridChunkCfg<D, 6>::kThreads;
   if (p->nchunks > 0) {
     if (all_j_equal(p->g, 6)) {
       cudaError_t e = cudaFuncSetAttribute(k_gridding_chunk<D, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      k_gridding_chunk<D, 6><<<(unsigned)p->nchunks, 256, smem, p->stream>>>(y, p->tiles, p->chunks, P, p->g);
+      k_gridding_chunk<D, 6><<<(unsigned)p->nchunks, NT, smem, p->stream>>>(y, p->tiles, p->chunks, P, p->g);
     } else {
       cudaError_t e = cudaFuncSetAttribute(k_gridding_chunk<D, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      k_gridding_chunk<D, 0><<<(unsigned)p->nchunks, 256, smem, p->stream>>>(y, p->tiles, p->chunks, P, p->g);
+      k_gridding_chunk<D, 0><<<(unsigned)p->nchunks, NT, smem, p->stream>>>(y, p->tiles, p->chunks, P, p->g);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -303,15 +330,16 @@ template <int D>
 cudaError_t gridding_static_d(const nufft_plan_t* p, const float2* y, float2* grid, float2* tiles) {
   const Points P = points_view(p);
   const size_t smem = (size_t)p->g.padded_cells * sizeof(float2);
+  constexpr int NT = GridChunkCfg<D, 6>::kThreads;
   if (p->nchunks > 0) {
     if (all_j_equal(p->g, 6)) {
       cudaError_t e = cudaFuncSetAttribute(k_gridding_chunk<D, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      k_gridding_chunk<D, 6><<<(unsigned)p->nchunks, 256, smem, p->stream>>>(y, tiles, p->chunks, P, p->g);
+      k_gridding_chunk<D, 6><<<(unsigned)p->nchunks, NT, smem, p->stream>>>(y, tiles, p->chunks, P, p->g);
     } else {
       cudaError_t e = cudaFuncSetAttribute(k_gridding_chunk<D, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      k_gridding_chunk<D, 0><<<(unsigned)p->nchunks, 256, smem, p->stream>>>(y, tiles, p->chunks, P, p->g);
+      k_gridding_chunk<D, 0><<<(unsigned)p->nchunks, NT, smem, p->stream>>>(y, tiles, p->chunks, P, p->g);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

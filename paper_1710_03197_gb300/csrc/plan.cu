@@ -456,11 +456,11 @@ int build_plan(nufft_plan_t* p, const float* om) {
   std::vector<int32_t> bc(g.nbins + 1);
   for (int64_t b = 0; b < g.nbins; ++b) {
     bc[b] = (int32_t)ch.size();
-    for (int32_t s0 = bs[b]; s0 < bs[b + 1]; s0 += kChunkPoints) {
+    for (int32_t s0 = bs[b]; s0 < bs[b + 1]; s0 += kChunkPoints[d]) {
       Chunk c;
       c.bin = (int32_t)b;
       c.start = s0;
-      c.count = std::min<int32_t>(kChunkPoints, bs[b + 1] - s0);
+      c.count = std::min<int32_t>(kChunkPoints[d], bs[b + 1] - s0);
       c.pad = 0;
       ch.push_back(c);
     }
@@ -512,6 +512,8 @@ extern "C" int nufft_plan(int d, const int* Nd, const int* Kd, const int* Jd, in
     g.T[a] = std::min(base_tile, K);
     g.nb[a] = K / g.T[a];
     g.P[a] = g.T[a] + J - 1;
+    while ((1 << g.lT[a]) < g.T[a]) ++g.lT[a];
+    while ((1 << g.lnb[a]) < g.nb[a]) ++g.lnb[a];
   }
   int64_t stride = 1;
   g.nbins = 1;
