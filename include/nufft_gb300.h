@@ -57,9 +57,11 @@ typedef struct nufft_plan nufft_plan_t;
  * (reciprocal Kaiser-Bessel transform, alpha = 2.34 J), the J x J min-max
  * matrix inverse per dimension, and per point and dimension the first
  * neighbour and the J interpolation coefficients (stored as complex64).
- * Points are then sorted by grid tile (counting sort by tile, stable in m),
- * which replaces the paper's CSR matrix and pre-indexes (Section 2.1.2,
- * Section 2.2.3) with per-point records read by the kernels.
+ * Points are then sorted by grid tile (stable radix sort by tile), each tile's
+ * points are cut into chunks, and the points inside a chunk are reordered so
+ * that the points sharing a warp instruction in the gridding kernel hit
+ * disjoint shared-memory banks.  This replaces the paper's CSR matrix and
+ * pre-indexes (Section 2.1.2, Section 2.2.3) with per-point records.
  *
  *   d       number of dimensions, 1..3
  *   Nd      image size per dimension (d ints): even, 2 <= N_i <= K_i

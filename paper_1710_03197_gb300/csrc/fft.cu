@@ -92,19 +92,22 @@ __device__ __forceinline__ void dft(float2* v) {
 constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
 
 // Shared-memory position of element p of the line owned by lane-group b.
+// Contiguous axis: one line after another, one pad word per 8 elements.
+// Strided axis: W lines side by side (W consecutive grid columns), row pitch W+1.
 template <int L, bool STRIDED>
-struct SmemIdx {
-  static constexpr int kB = STRIDED ? 8 : ((L / 8) >= 256 ? 1 : 256 / (L / 8));
-  static constexpr int kLinePitch = L + L / 8;          // contiguous layout, one pad per 8
-  static constexpr int kWords = STRIDED ? L * (kB + 1) : kB * kLinePitch;
-  __device__ __forceinline__ static int at(int b, int p) {
-    return STRIDED ? p * (kB + 1) + b : b * kLinePitch + p + (p >> 3);
+struct SmemMap {
+  int w;  // lines per CTA
+  static constexpr int kLinePitch = L + L / 8;
+  __device__ __forceinline__ int at(int b, int p) const {
+    return STRIDED ? p * (w + 1) + b : b * kLinePitch + p + (p >> 3);
   }
+  static size_t words(int w) { return STRIDED ? (size_t)L * (w + 1) : (size_t)w * kLinePitch; }
 };
 
 // One Stockham stage of radix R over span Ns, in place in shared memory.
 template <int L, bool STRIDED, bool INV, int R>
-__device__ __forceinline__ void stage(float2* sm, int b, int t, int Ns, const float2* __restrict__ tw) {
+__device__ __forceinline__ void stage(float2* sm, const SmemMap<L, STRIDED> SI, int b, int t, int Ns,
+                                      const float2* __restrict__ tw) {
   constexpr int TPL = L / 8;
   constexpr int Q = 8 / R;
   float2 v[Q][R];
@@ -112,7 +115,7 @@ __device__ __forceinline__ void stage(float2* sm, int b, int t, int Ns, const fl
   for (int q = 0; q < Q; ++q) {
     const int j = t + q * TPL;
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[q][r] = sm[SmemIdx<L, STRIDED>::at(b, j + r * (L / R))];
+    for (int r = 0; r < R; ++r) v[q][r] = sm[SI.at(b, j + r * (L / R))];
   }
   __syncthreads();
 #pragma unroll
@@ -131,32 +134,31 @@ __device__ __forceinline__ void stage(float2* sm, int b, int t, int Ns, const fl
     dft<R, INV>(v[q]);
     const int base = (j - k) * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) sm[SmemIdx<L, STRIDED>::at(b, base + r * Ns)] = v[q][r];
+    for (int r = 0; r < R; ++r) sm[SI.at(b, base + r * Ns)] = v[q][r];
   }
   __syncthreads();
 }
 
 template <int L, bool STRIDED, bool INV>
 __global__ void __launch_bounds__(STRIDED ? L : 256)
-k_fft_pass(const FftArgs A) {
-  using SI = SmemIdx<L, STRIDED>;
+k_fft_pass(const FftArgs A, const int W) {
   constexpr int TPL = L / 8;
-  constexpr int B = SI::kB;
+  const SmemMap<L, STRIDED> SI{W};
   extern __shared__ float2 sm[];
 
   const int tid = threadIdx.x;
   int b, t;
   int64_t o, in;
   if (STRIDED) {
-    b = tid & 7;
-    t = tid >> 3;
-    const int64_t nib = A.inner >> 3;
+    b = tid % W;
+    t = tid / W;
+    const int64_t nib = A.inner / W;
     o = blockIdx.x / nib;
-    in = (blockIdx.x % nib) * 8 + b;
+    in = (blockIdx.x % nib) * W + b;
   } else {
     b = tid / TPL;
     t = tid % TPL;
-    o = (int64_t)blockIdx.x * B + b;
+    o = (int64_t)blockIdx.x * W + b;
     in = 0;
   }
   const bool live = o < A.nouter;
@@ -197,7 +199,7 @@ k_fft_pass(const FftArgs A) {
         v = A.src[goff + (int64_t)p * stride + in];
       }
     }
-    sm[SI::at(b, p)] = v;
+    sm[SI.at(b, p)] = v;
   }
   __syncthreads();
 
@@ -205,17 +207,17 @@ k_fft_pass(const FftArgs A) {
   constexpr int LOG = ilog2(L);
   constexpr int R0 = 1 << (LOG % 3);
   int Ns = 1;
-  if (R0 == 2) { stage<L, STRIDED, INV, 2>(sm, b, t, Ns, A.tw); Ns *= 2; }
-  if (R0 == 4) { stage<L, STRIDED, INV, 4>(sm, b, t, Ns, A.tw); Ns *= 4; }
+  if (R0 == 2) { stage<L, STRIDED, INV, 2>(sm, SI, b, t, Ns, A.tw); Ns *= 2; }
+  if (R0 == 4) { stage<L, STRIDED, INV, 4>(sm, SI, b, t, Ns, A.tw); Ns *= 4; }
 #pragma unroll
-  for (int s = 0; s < LOG / 3; ++s) { stage<L, STRIDED, INV, 8>(sm, b, t, Ns, A.tw); Ns *= 8; }
+  for (int s = 0; s < LOG / 3; ++s) { stage<L, STRIDED, INV, 8>(sm, SI, b, t, Ns, A.tw); Ns *= 8; }
 
   // ---- store (pruned on the inverse side)
   if (!live) return;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const int p = t + k * TPL;
-    const float2 v = sm[SI::at(b, p)];
+    const float2 v = sm[SI.at(b, p)];
     if (!INV) {
       A.dst[goff + (int64_t)p * stride + in] = v;
     } else {
@@ -231,28 +233,34 @@ k_fft_pass(const FftArgs A) {
   }
 }
 
+// Lines per CTA: as many as give 256 threads (8 columns on a strided axis, for
+// 64-byte row segments), fewer when that would leave the GPU with fewer than
+// two CTAs per SM.
+constexpr int64_t kTargetBlocks = 2 * 152;
+
 template <int L, bool STRIDED, bool INV>
 cudaError_t launch_L(const FftArgs& A, cudaStream_t st) {
-  using SI = SmemIdx<L, STRIDED>;
-  const size_t smem = (size_t)SI::kWords * sizeof(float2);
-  static bool attr_set = false;  // per process; the attribute is per function
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_fft_pass<L, STRIDED, INV>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  constexpr int TPL = L / 8;
+  int W;
   int64_t blocks;
-  int threads;
   if (STRIDED) {
-    blocks = A.nouter * (A.inner / 8);
-    threads = L;  // 8 lines x L/8 threads
+    W = 8;
+    while (W > 2 && A.nouter * (A.inner / W) < kTargetBlocks) W >>= 1;
+    blocks = A.nouter * (A.inner / W);
   } else {
-    blocks = (A.nouter + SI::kB - 1) / SI::kB;
-    threads = SI::kB * (L / 8);
+    W = TPL >= 256 ? 1 : 256 / TPL;
+    while (W > 1 && (A.nouter + W - 1) / W < kTargetBlocks) W >>= 1;
+    blocks = (A.nouter + W - 1) / W;
+  }
+  const int threads = W * TPL;
+  const size_t smem = SmemMap<L, STRIDED>::words(W) * sizeof(float2);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_fft_pass<L, STRIDED, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
   }
   if (blocks == 0) return cudaSuccess;
-  k_fft_pass<L, STRIDED, INV><<<(unsigned)blocks, threads, smem, st>>>(A);
+  k_fft_pass<L, STRIDED, INV><<<(unsigned)blocks, threads, smem, st>>>(A, W);
   return cudaGetLastError();
 }
 

@@ -138,6 +138,9 @@ k_gridding_chunk(const float2* __restrict__ y, float2* __restrict__ tiles, const
   const int P1 = D > 1 ? g.P[1] : 1;
   const int P2 = D > 2 ? g.P[2] : 1;
 
+  // Consecutive points of the chunk share a warp instruction: the plan orders
+  // each chunk so that every aligned group of per_warp points covers disjoint
+  // shared-memory bank windows (see the bank-order kernel in plan.cu).
   if (sub < per_warp) {
     for (int q = warp * per_warp + sub; q < ch.count; q += nwarps * per_warp) {
       const int64_t i = (int64_t)ch.start + q;
@@ -239,7 +242,9 @@ k_gridding_reduce(const float2* __restrict__ tiles, const int32_t* __restrict__ 
       lc[1] = (c >> g.lT[2]) & (T1 - 1);
       lc[0] = c >> (g.lT[2] + g.lT[1]);
     }
-    float2 acc = make_float2(0.f, 0.f);
+    // First chunk of every contributing neighbour: all loads issued together.
+    int locs[1 << D];
+    float2 first[1 << D];
 #pragma unroll
     for (int e = 0; e < (1 << D); ++e) {
       int la[3] = {0, 0, 0};
@@ -250,10 +255,17 @@ k_gridding_reduce(const float2* __restrict__ tiles, const int32_t* __restrict__ 
         la[a] = lc[a] + (ea ? g.T[a] : 0);
         ok = ok && (la[a] < g.P[a]);
       }
-      if (!ok) continue;
-      const int loc = D == 1 ? la[0] : (D == 2 ? la[0] * P1 + la[1] : (la[0] * P1 + la[1]) * P2 + la[2]);
+      locs[e] = ok ? (D == 1 ? la[0] : (D == 2 ? la[0] * P1 + la[1] : (la[0] * P1 + la[1]) * P2 + la[2])) : -1;
+      first[e] = (locs[e] >= 0 && s_q0[e] < s_q1[e]) ? __ldg(&tiles[(int64_t)s_q0[e] * pc + locs[e]])
+                                                      : make_float2(0.f, 0.f);
+    }
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int e = 0; e < (1 << D); ++e) {
+      acc = cadd(acc, first[e]);
+      if (locs[e] < 0) continue;
       const int q1 = s_q1[e];
-      for (int q = s_q0[e]; q < q1; ++q) acc = cadd(acc, __ldg(&tiles[(int64_t)q * pc + loc]));
+      for (int q = s_q0[e] + 1; q < q1; ++q) acc = cadd(acc, __ldg(&tiles[(int64_t)q * pc + locs[e]]));
     }
     int64_t off = 0;
     for (int a = 0; a < D; ++a) off += (int64_t)((bc[a] << g.lT[a]) + lc[a]) * g.Kstride[a];

@@ -329,6 +329,73 @@ __global__ void k_coefficients(const float* om, Geom g, int64_t M, const int32_t
   kf_out[(int64_t)a * M + i] = wrap_first(k0, K);
 }
 
+// Order each chunk's points for the gridding kernel.  Lane groups of J_last
+// lanes handle one point each and G = 32 / J_last consecutive points share a
+// warp instruction; point p's atomics for neighbour tap (j_0..j_{d-1}) land on
+// the J_last consecutive shared-memory banks starting at
+//   (cell index of its first neighbour in the padded tile + tap offset) mod 32,
+// and the tap offset is the same for all points of an instruction.  So a
+// group of G points whose first-neighbour windows [b, b + J_last) mod 32 are
+// disjoint is free of bank conflicts for every one of its taps.  One thread
+// per chunk buckets the points by b and forms the groups greedily, taking
+// from the fullest bucket whose window is still free (a conflicting point
+// only when no free window is left); stable and deterministic.
+__global__ void k_bank_order(const float* om, Geom g, const Chunk* chunks, int64_t nchunks, const int32_t* perm_in,
+                             int32_t* perm_out, int32_t* next) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= nchunks) return;
+  const Chunk ch = chunks[c];
+  const int d = g.d;
+  const int JL = g.J[d - 1];
+  const int G = 32 / JL;
+  const unsigned base_mask = JL >= 32 ? 0xffffffffu : ((1u << JL) - 1u);
+  int org[kMaxDim];
+  {
+    int rem = ch.bin;
+    for (int a = d - 1; a >= 0; --a) {
+      org[a] = (rem % g.nb[a]) * g.T[a];
+      rem /= g.nb[a];
+    }
+  }
+  int head[32], tail[32], cnt[32];
+  for (int k = 0; k < 32; ++k) { head[k] = -1; tail[k] = -1; cnt[k] = 0; }
+  for (int q = 0; q < ch.count; ++q) {
+    const int64_t i = (int64_t)ch.start + q;
+    const int64_t m = perm_in[i];
+    int cell = 0;
+    for (int a = 0; a < d; ++a) {
+      const int kf = wrap_first(offset_k0((double)om[m * d + a], g.K[a], g.J[a]), g.K[a]);
+      cell = cell * g.P[a] + (kf - org[a]);
+    }
+    const int b = cell & 31;
+    next[i] = -1;
+    if (tail[b] >= 0) next[(int64_t)ch.start + tail[b]] = q; else head[b] = q;
+    tail[b] = q;
+    ++cnt[b];
+  }
+  int out = 0;
+  while (out < ch.count) {
+    unsigned used = 0u;
+    for (int s = 0; s < G && out < ch.count; ++s) {
+      int best = -1;
+      for (int k = 0; k < 32; ++k) {
+        if (cnt[k] == 0) continue;
+        const unsigned win = (base_mask << k) | (k ? (base_mask >> (32 - k)) : 0u);
+        if ((win & used) == 0u && (best < 0 || cnt[k] > cnt[best])) best = k;
+      }
+      if (best < 0)
+        for (int k = 0; k < 32; ++k)
+          if (cnt[k] > 0 && (best < 0 || cnt[k] > cnt[best])) best = k;
+      const int q = head[best];
+      head[best] = next[(int64_t)ch.start + q];
+      --cnt[best];
+      used |= (base_mask << best) | (best ? (base_mask >> (32 - best)) : 0u);
+      perm_out[(int64_t)ch.start + out] = perm_in[(int64_t)ch.start + q];
+      ++out;
+    }
+  }
+}
+
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 template <class T>
@@ -434,21 +501,6 @@ int build_plan(nufft_plan_t* p, const float* om) {
     NUFFT_CUDA_TRY(p, cudaMemsetAsync(p->bin_start, 0, (g.nbins + 1) * sizeof(int32_t), st));
   }
 
-  // ---- per-point interpolator in sorted order
-  int64_t coef_tot = 0;
-  for (int a = 0; a < d; ++a) { p->coef_off[a] = coef_tot; coef_tot += (int64_t)g.J[a] * M; }
-  NUFFT_CUDA_TRY(p, dalloc(p, &p->kf, M * d));
-  NUFFT_CUDA_TRY(p, dalloc(p, &p->coef, coef_tot));
-  if (M > 0) {
-    const int64_t n = M * d;
-    k_coefficients<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(om, g, M, p->perm, s64, D, Tinv, p->kf, p->coef,
-                                                               p->coef_off[0], p->coef_off[1], p->coef_off[2]);
-    NUFFT_CUDA_TRY(p, cudaGetLastError());
-  }
-  NUFFT_CUDA_TRY(p, cudaMemcpyAsync(hflag, flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-  NUFFT_CUDA_TRY(p, cudaStreamSynchronize(st));
-  if (hflag[1]) return set_error(p, NUFFT_EINVAL, "min-max matrix G is singular for these sizes");
-
   // ---- gridding work list: each tile's points cut into chunks
   std::vector<int32_t> bs(g.nbins + 1);
   NUFFT_CUDA_TRY(p, cudaMemcpy(bs.data(), p->bin_start, (g.nbins + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
@@ -472,6 +524,34 @@ int build_plan(nufft_plan_t* p, const float* om) {
   if (p->nchunks > 0)
     NUFFT_CUDA_TRY(p, cudaMemcpy(p->chunks, ch.data(), ch.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
   NUFFT_CUDA_TRY(p, cudaMemcpy(p->bin_chunk, bc.data(), bc.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+
+  // ---- order the points of each chunk for conflict-free shared-memory atomics
+  if (M > 0 && p->nchunks > 0) {
+    int32_t *perm2 = nullptr, *nxt = nullptr;
+    NUFFT_CUDA_TRY(p, cudaMalloc((void**)&perm2, M * sizeof(int32_t)));
+    struct G2 { void* a; ~G2() { if (a) cudaFree(a); } } g2{perm2};
+    NUFFT_CUDA_TRY(p, cudaMalloc((void**)&nxt, M * sizeof(int32_t)));
+    struct G3 { void* a; ~G3() { if (a) cudaFree(a); } } g3{nxt};
+    k_bank_order<<<(unsigned)((p->nchunks + 63) / 64), 64, 0, st>>>(om, g, p->chunks, p->nchunks, p->perm, perm2, nxt);
+    NUFFT_CUDA_TRY(p, cudaGetLastError());
+    NUFFT_CUDA_TRY(p, cudaMemcpyAsync(p->perm, perm2, M * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    NUFFT_CUDA_TRY(p, cudaStreamSynchronize(st));
+  }
+
+  // ---- per-point interpolator in sorted order
+  int64_t coef_tot = 0;
+  for (int a = 0; a < d; ++a) { p->coef_off[a] = coef_tot; coef_tot += (int64_t)g.J[a] * M; }
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->kf, M * d));
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->coef, coef_tot));
+  if (M > 0) {
+    const int64_t n = M * d;
+    k_coefficients<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(om, g, M, p->perm, s64, D, Tinv, p->kf, p->coef,
+                                                               p->coef_off[0], p->coef_off[1], p->coef_off[2]);
+    NUFFT_CUDA_TRY(p, cudaGetLastError());
+  }
+  NUFFT_CUDA_TRY(p, cudaMemcpyAsync(hflag, flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  NUFFT_CUDA_TRY(p, cudaStreamSynchronize(st));
+  if (hflag[1]) return set_error(p, NUFFT_EINVAL, "min-max matrix G is singular for these sizes");
 
   // ---- work space
   NUFFT_CUDA_TRY(p, dalloc(p, &p->tiles, p->nchunks * g.padded_cells));
