@@ -19,7 +19,7 @@ constexpr int kMaxK = 1024;
 // chunks of at most this many so that a dense tile (the centre of a radial
 // trajectory) is spread over several CTAs, and small problems still fill the
 // GPU.  3D chunks are larger because each partial tile costs 74 KB.
-constexpr int kChunkPoints[4] = {0, 1024, 512, 2048};
+constexpr int kChunkPoints[4] = {0, 1024, 256, 2048};
 
 // Geometry of the oversampled grid and of the tile decomposition.
 struct Geom {

@@ -20,6 +20,7 @@
 // of the padded tiles that cover it (its own tile's chunks and those of the
 // 2^d - 1 lower neighbour tiles).  No global atomics; every grid cell is
 // written exactly once.
+#include <algorithm>
 #include <mutex>
 
 #include "internal.cuh"
@@ -57,7 +58,7 @@ k_interp(const float2* __restrict__ grid, float2* __restrict__ y, const Points P
       for (int j0 = 0; j0 < (JF > 0 ? JF : kMaxJ); ++j0) {
         if (JF == 0 && j0 >= J0) break;
         const float2 c0 = P.coef[P.coef_off[0] + (int64_t)j0 * P.M + i];
-        const int64_t row = (int64_t)((k0 + j0) & (g.K[0] - 1)) * g.Kstride[0];
+        const int row = ((k0 + j0) & (g.K[0] - 1)) * (int)g.Kstride[0];
         acc = cadd(acc, cmul(c0, __ldg(&grid[row + gl])));
       }
       part = cmul(cl, acc);
@@ -70,17 +71,23 @@ k_interp(const float2* __restrict__ grid, float2* __restrict__ y, const Points P
         if (JF == 0 && j1 >= J1) break;
         c1v[j1] = P.coef[P.coef_off[1] + (int64_t)j1 * P.M + i];
       }
+      // row offsets of the J1 neighbour rows within a plane (32-bit: K^d < 2^31)
+      int rowoff[JF > 0 ? JF : kMaxJ];
+#pragma unroll
+      for (int j1 = 0; j1 < (JF > 0 ? JF : kMaxJ); ++j1) {
+        if (JF == 0 && j1 >= J1) break;
+        rowoff[j1] = ((k1 + j1) & (g.K[1] - 1)) * (int)g.Kstride[1] + gl;
+      }
       float2 acc = make_float2(0.f, 0.f);
 #pragma unroll 1
       for (int j0 = 0; j0 < J0; ++j0) {
         const float2 c0 = P.coef[P.coef_off[0] + (int64_t)j0 * P.M + i];
-        const int64_t plane = (int64_t)((k0 + j0) & (g.K[0] - 1)) * g.Kstride[0];
+        const float2* plane = grid + ((k0 + j0) & (g.K[0] - 1)) * (int)g.Kstride[0];
         float2 acc1 = make_float2(0.f, 0.f);
 #pragma unroll
         for (int j1 = 0; j1 < (JF > 0 ? JF : kMaxJ); ++j1) {
           if (JF == 0 && j1 >= J1) break;
-          const int64_t row = plane + (int64_t)((k1 + j1) & (g.K[1] - 1)) * g.Kstride[1];
-          acc1 = cadd(acc1, cmul(c1v[j1], __ldg(&grid[row + gl])));
+          acc1 = cadd(acc1, cmul(c1v[j1], __ldg(&plane[rowoff[j1]])));
         }
         acc = cadd(acc, cmul(c0, acc1));
       }
@@ -199,38 +206,51 @@ k_gridding_chunk(const float2* __restrict__ y, float2* __restrict__ tiles, const
 // ---------------------------------------------------------------- gridding, tile reduction
 // One CTA per tile: grid cell c of tile b is the sum over e in {0,1}^d of the
 // padded tiles of bin b - e (wrapped per dimension) at local position
-// c - origin(b) + e * T, when that position lies inside the padded tile.  The
-// sum runs over e, then over the source bin's chunks, in a fixed order.
-template <int D>
-__global__ void __launch_bounds__(256)
+// c - origin(b) + e * T, when that position lies inside the padded tile.  Each
+// thread owns CPT cells of the tile; their padded-tile offset and the mask of
+// neighbours e that reach them are computed once, so every (e, chunk) pair
+// costs one predicated load per cell.  The sum runs over e, then over the
+// source bin's chunks, in a fixed order.
+template <int D, int CPT>
+__global__ void __launch_bounds__(1024)
 k_gridding_reduce(const float2* __restrict__ tiles, const int32_t* __restrict__ bin_chunk,
                   float2* __restrict__ grid, const Geom g) {
-  __shared__ int s_q0[1 << kMaxDim], s_q1[1 << kMaxDim];
+  __shared__ int s_q0[1 << kMaxDim], s_q1[1 << kMaxDim], s_delta[1 << kMaxDim];
   const int bin = blockIdx.x;
   int bc[kMaxDim];
   {
     int rem = bin;
+#pragma unroll
     for (int a = D - 1; a >= 0; --a) {
       bc[a] = rem & (g.nb[a] - 1);
       rem >>= g.lnb[a];
     }
   }
+  const int P1 = D > 1 ? g.P[1] : 1, P2 = D > 2 ? g.P[2] : 1;
   if (threadIdx.x < (1 << D)) {
     const int e = threadIdx.x;
-    int src = 0;
+    int src = 0, delta = 0;
     for (int a = 0; a < D; ++a) {
       const int ea = (e >> (D - 1 - a)) & 1;
       src = (src << g.lnb[a]) | ((bc[a] - ea) & (g.nb[a] - 1));
+      const int pstride = a == D - 1 ? 1 : (a == D - 2 ? g.P[D - 1] : P1 * P2);
+      delta += ea * g.T[a] * pstride;
     }
     s_q0[e] = bin_chunk[src];
     s_q1[e] = bin_chunk[src + 1];
+    s_delta[e] = delta;
   }
   __syncthreads();
-  const int T0 = g.T[0], T1 = D > 1 ? g.T[1] : 1, T2 = D > 2 ? g.T[2] : 1;
-  const int P1 = D > 1 ? g.P[1] : 1, P2 = D > 2 ? g.P[2] : 1;
-  const int tile_cells = T0 * T1 * T2;
-  const int64_t pc = g.padded_cells;
-  for (int c = threadIdx.x; c < tile_cells; c += blockDim.x) {
+  const int T1 = D > 1 ? g.T[1] : 1, T2 = D > 2 ? g.T[2] : 1;
+  int loc0[CPT];
+  unsigned emask[CPT];
+  int goff[CPT];
+  float2 acc[CPT];
+  int tile_cells = 1;
+  for (int a = 0; a < D; ++a) tile_cells *= g.T[a];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int c = min((int)(threadIdx.x + k * blockDim.x), tile_cells - 1);
     int lc[3] = {0, 0, 0};
     if (D == 1) {
       lc[0] = c;
@@ -242,35 +262,48 @@ k_gridding_reduce(const float2* __restrict__ tiles, const int32_t* __restrict__ 
       lc[1] = (c >> g.lT[2]) & (T1 - 1);
       lc[0] = c >> (g.lT[2] + g.lT[1]);
     }
-    // First chunk of every contributing neighbour: all loads issued together.
-    int locs[1 << D];
-    float2 first[1 << D];
+    loc0[k] = D == 1 ? lc[0] : (D == 2 ? lc[0] * P1 + lc[1] : (lc[0] * P1 + lc[1]) * P2 + lc[2]);
+    unsigned m = 0;
 #pragma unroll
     for (int e = 0; e < (1 << D); ++e) {
-      int la[3] = {0, 0, 0};
       bool ok = true;
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        const int ea = (e >> (D - 1 - a)) & 1;
-        la[a] = lc[a] + (ea ? g.T[a] : 0);
-        ok = ok && (la[a] < g.P[a]);
-      }
-      locs[e] = ok ? (D == 1 ? la[0] : (D == 2 ? la[0] * P1 + la[1] : (la[0] * P1 + la[1]) * P2 + la[2])) : -1;
-      first[e] = (locs[e] >= 0 && s_q0[e] < s_q1[e]) ? __ldg(&tiles[(int64_t)s_q0[e] * pc + locs[e]])
-                                                      : make_float2(0.f, 0.f);
+      for (int a = 0; a < D; ++a)
+        if ((e >> (D - 1 - a)) & 1) ok = ok && (lc[a] + g.T[a] < g.P[a]);
+      m |= (ok ? 1u : 0u) << e;
     }
-    float2 acc = make_float2(0.f, 0.f);
+    emask[k] = ((int)(threadIdx.x + k * blockDim.x) < tile_cells) ? m : 0u;
+    int off = 0;
 #pragma unroll
-    for (int e = 0; e < (1 << D); ++e) {
-      acc = cadd(acc, first[e]);
-      if (locs[e] < 0) continue;
-      const int q1 = s_q1[e];
-      for (int q = s_q0[e] + 1; q < q1; ++q) acc = cadd(acc, __ldg(&tiles[(int64_t)q * pc + locs[e]]));
-    }
-    int64_t off = 0;
-    for (int a = 0; a < D; ++a) off += (int64_t)((bc[a] << g.lT[a]) + lc[a]) * g.Kstride[a];
-    grid[off] = acc;
+    for (int a = 0; a < D; ++a) off += ((bc[a] << g.lT[a]) + lc[a]) * (int)g.Kstride[a];
+    goff[k] = off;
+    acc[k] = make_float2(0.f, 0.f);
   }
+  const int64_t pc = g.padded_cells;
+  for (int e = 0; e < (1 << D); ++e) {
+    const int q1 = s_q1[e];
+    const int delta = s_delta[e];
+    for (int q = s_q0[e]; q < q1; ++q) {
+      const float2* src = tiles + (int64_t)q * pc + delta;
+#pragma unroll
+      for (int k = 0; k < CPT; ++k)
+        if ((emask[k] >> e) & 1u) acc[k] = cadd(acc[k], __ldg(&src[loc0[k]]));
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < CPT; ++k)
+    if ((int)(threadIdx.x + k * blockDim.x) < tile_cells) grid[goff[k]] = acc[k];
+}
+
+// The reduction gives every thread 4 cells of the tile (tile cells / 4 threads).
+template <int D>
+cudaError_t launch_reduce(const nufft_plan_t* p, const float2* tiles, float2* grid) {
+  int cells = 1;
+  for (int a = 0; a < D; ++a) cells *= p->g.T[a];
+  const int threads = std::max(32, std::min(1024, cells / 4));
+  if ((int64_t)threads * 4 < cells) return cudaErrorInvalidValue;
+  k_gridding_reduce<D, 4><<<(unsigned)p->g.nbins, threads, 0, p->stream>>>(tiles, p->bin_chunk, grid, p->g);
+  return cudaGetLastError();
 }
 
 bool all_j_equal(const Geom& g, int J) {
@@ -310,8 +343,7 @@ cudaError_t gridding_d(const nufft_plan_t* p, const float2* y, float2* grid) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  k_gridding_reduce<D><<<(unsigned)p->g.nbins, 256, 0, p->stream>>>(p->tiles, p->bin_chunk, grid, p->g);
-  return cudaGetLastError();
+  return launch_reduce<D>(p, p->tiles, grid);
 }
 
 // ---------------------------------------------------------------- gridding without allocation
@@ -356,8 +388,7 @@ cudaError_t gridding_static_d(const nufft_plan_t* p, const float2* y, float2* gr
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  k_gridding_reduce<D><<<(unsigned)p->g.nbins, 256, 0, p->stream>>>(tiles, p->bin_chunk, grid, p->g);
-  return cudaGetLastError();
+  return launch_reduce<D>(p, tiles, grid);
 }
 
 }  // namespace

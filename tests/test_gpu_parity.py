@@ -111,7 +111,7 @@ def test_tile_sort_and_bank_order(case):
     # whenever the run's points allow it (greedy): check the groups are no worse
     # than the plain trajectory order, and that each chunk holds the same points
     # as the stable (trajectory-order) sort would.
-    C = {1: 1024, 2: 512, 3: 2048}[d]
+    C = {1: 1024, 2: 256, 3: 2048}[d]
     JL = case["Jd"][-1]
     G = 32 // JL
     P = [t + j - 1 for t, j in zip(T, case["Jd"])]
