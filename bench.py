@@ -155,10 +155,15 @@ WORKLOAD_TEXT = {
 }
 
 
-def run_workload(nf, torch, name: str, steps: int, warmup: int, dev, flush_bytes: int):
-    spec, om, x, _ = W.make_workload(name)
+def run_workload(nf, torch, name: str, steps: int, warmup: int, dev, flush_bytes: int, solvers: bool = False):
+    spec, om, x, noise = W.make_workload(name)
     M = spec["M"]
-    plan = nf.NufftPlan(torch.from_numpy(om).to(dev), spec["Nd"], spec["Kd"], spec["Jd"])
+    om_d = torch.from_numpy(om).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan = nf.NufftPlan(om_d, spec["Nd"], spec["Kd"], spec["Jd"])
+    torch.cuda.synchronize()
+    plan_ms = (time.perf_counter() - t0) * 1e3
     info = plan.info()
     xd = torch.from_numpy(x).to(dev)
     grid = torch.empty(spec["Kd"], dtype=torch.complex64, device=dev)
@@ -211,6 +216,37 @@ def run_workload(nf, torch, name: str, steps: int, warmup: int, dev, flush_bytes
         e1.synchronize()
         mono.append(e0.elapsed_time(e1))
 
+    # the self-adjoint operator A^H A (one call per step, L2 flushed between)
+    sa = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0.record(stream)
+        plan.selfadjoint(xd, xo)
+        e1.record(stream)
+        e1.synchronize()
+        sa.append(e0.elapsed_time(e1))
+    rows = {"a1_plan_ms": round(plan_ms, 3), "a8_selfadjoint_ms": round(statistics.mean(sa), 5)}
+    if solvers:
+        # the reconstruction runs of the paper's solvers on this workload's data
+        yd = plan.forward(xd)
+        if noise is not None:
+            yd = yd + torch.from_numpy(noise).to(dev)
+        yd = yd.contiguous()
+        x0 = torch.zeros(spec["Nd"], dtype=torch.complex64, device=dev)
+        plan.solve_cg(yd, x0.clone(), maxiter=2)
+        for key, fn in (("a9_cg_100_iterations_ms", lambda: plan.solve_cg(yd, x0.clone(), maxiter=100)),
+                        ("a9_l1tv_ols_50_iterations_ms",
+                         lambda: plan.solve_l1tv_ols(yd, x0.clone(), maxiter=50, inner=2, cg_iters=5, mu=1.0, lam=0.01)),
+                        ("a9_l1tv_lad_50_iterations_ms",
+                         lambda: plan.solve_l1tv_lad(yd, x0.clone(), maxiter=50, inner=2, cg_iters=5, mu=1.0, lam=0.01))):
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            rows[key] = round(e0.elapsed_time(e1), 3)
+        rows["a9_solver_settings"] = "CG x0=0; L1TV: inner=2, cg_iters=5, mu=1, lambda=0.01"
+
     # end to end through the host-buffer entry points (pinned host memory)
     x_h = torch.from_numpy(x).pin_memory()
     y_h = torch.empty(M, dtype=torch.complex64).pin_memory()
@@ -226,7 +262,7 @@ def run_workload(nf, torch, name: str, steps: int, warmup: int, dev, flush_bytes
     nprod = int(np.prod(spec["Nd"]))
     plan.close()
     return dict(spec=spec, info=info, step_ms=step_ms, stage_ms=stage_ms, mono_ms=mono, e2e_s=e2e_s,
-                h2d=8 * (nprod + M), d2h=8 * (M + nprod))
+                h2d=8 * (nprod + M), d2h=8 * (M + nprod), rows=rows)
 
 
 def roofline_for(res, peak_gbs: float, peak_kind: str, traffic: dict):
@@ -265,7 +301,8 @@ def ours(args):
         torch.distributed.barrier()
     names = [w.strip() for w in args.workloads.split(",") if w.strip()]
     with ClockSampler(torch.cuda.current_device() if world == 1 else local, clocks_path) as clk:
-        results = {n: run_workload(nf, torch, n, args.steps, args.warmup, dev, flush_bytes) for n in names}
+        results = {n: run_workload(nf, torch, n, args.steps, args.warmup, dev, flush_bytes,
+                                   solvers=(i == 0 and not args.no_solvers)) for i, n in enumerate(names)}
     torch.cuda.synchronize()
     res2 = results[names[0]]
     res3 = results[names[1]] if len(names) > 1 else None
@@ -312,6 +349,7 @@ def ours(args):
         "roofline": roof2,
         "stages": stages2,
         "monolithic_ms_per_step": round(statistics.mean(res2["mono_ms"]), 5),
+        "rows": res2["rows"],
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }
@@ -323,7 +361,7 @@ def ours(args):
             "e2e": {"value": round(M3 / res3["e2e_s"], 1), "unit": UNIT, "h2d_bytes_per_step": res3["h2d"],
                     "d2h_bytes_per_step": res3["d2h"]},
             "gpu_launches": launches_per_step(res3["spec"], res3["info"]["nchunks"]) * args.steps,
-            "roofline": roof3, "stages": stages3,
+            "roofline": roof3, "stages": stages3, "rows": res3["rows"],
             "monolithic_ms_per_step": round(statistics.mean(res3["mono_ms"]), 5)}}
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -392,6 +430,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-solvers", action="store_true", help="skip the solver timings (rows a9)")
     ap.add_argument("--workloads", default="radial2d_256,kooshball3d_128",
                     help="comma list; the first sets value/roofline, the second is reported under 'also'")
     args = ap.parse_args(argv)

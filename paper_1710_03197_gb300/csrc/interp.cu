@@ -149,9 +149,22 @@ k_gridding_chunk(const float2* __restrict__ y, float2* __restrict__ tiles, const
   // each chunk so that every aligned group of per_warp points covers disjoint
   // shared-memory bank windows (see the bank-order kernel in plan.cu).
   if (sub < per_warp) {
-    for (int q = warp * per_warp + sub; q < ch.count; q += nwarps * per_warp) {
+    const int stepq = nwarps * per_warp;
+    int q = warp * per_warp + sub;
+    // 1D/2D: the dependent load (sample through the permutation) runs one
+    // point ahead; 3D has enough work per point to hide it and no registers
+    // to spare.
+    float2 y_next = make_float2(0.f, 0.f);
+    if (D < 3 && q < ch.count) y_next = __ldg(&y[P.perm[(int64_t)ch.start + q]]);
+    for (; q < ch.count; q += stepq) {
       const int64_t i = (int64_t)ch.start + q;
-      const float2 yv = __ldg(&y[P.perm[i]]);
+      float2 yv;
+      if (D < 3) {
+        yv = y_next;
+        if (q + stepq < ch.count) y_next = __ldg(&y[P.perm[i + stepq]]);
+      } else {
+        yv = __ldg(&y[P.perm[i]]);
+      }
       const int ll = P.kf[(int64_t)(D - 1) * P.M + i] - org[D - 1] + l;
       const float2 cl = P.coef[P.coef_off[D - 1] + (int64_t)l * P.M + i];
       const float2 yl = cmulc(cl, yv);  // conj(c_last) * y
@@ -214,7 +227,10 @@ k_gridding_chunk(const float2* __restrict__ y, float2* __restrict__ tiles, const
 template <int D, int CPT>
 __global__ void __launch_bounds__(1024)
 k_gridding_reduce(const float2* __restrict__ tiles, const int32_t* __restrict__ bin_chunk,
-                  float2* __restrict__ grid, const Geom g) {
+                  float2* __restrict__ grid, const Geom g, const int NG) {
+  // NG thread groups of blockDim/NG threads; group h takes every NG-th (e, chunk)
+  // pair, and the groups' sums are added in group order at the end.
+  extern __shared__ float2 part[];
   __shared__ int s_q0[1 << kMaxDim], s_q1[1 << kMaxDim], s_delta[1 << kMaxDim];
   const int bin = blockIdx.x;
   int bc[kMaxDim];
@@ -248,9 +264,12 @@ k_gridding_reduce(const float2* __restrict__ tiles, const int32_t* __restrict__ 
   float2 acc[CPT];
   int tile_cells = 1;
   for (int a = 0; a < D; ++a) tile_cells *= g.T[a];
+  const int gsize = blockDim.x / NG;
+  const int h = threadIdx.x / gsize;
+  const int tg = threadIdx.x - h * gsize;
 #pragma unroll
   for (int k = 0; k < CPT; ++k) {
-    const int c = min((int)(threadIdx.x + k * blockDim.x), tile_cells - 1);
+    const int c = min(tg + k * gsize, tile_cells - 1);
     int lc[3] = {0, 0, 0};
     if (D == 1) {
       lc[0] = c;
@@ -272,7 +291,7 @@ k_gridding_reduce(const float2* __restrict__ tiles, const int32_t* __restrict__ 
         if ((e >> (D - 1 - a)) & 1) ok = ok && (lc[a] + g.T[a] < g.P[a]);
       m |= (ok ? 1u : 0u) << e;
     }
-    emask[k] = ((int)(threadIdx.x + k * blockDim.x) < tile_cells) ? m : 0u;
+    emask[k] = (tg + k * gsize < tile_cells) ? m : 0u;
     int off = 0;
 #pragma unroll
     for (int a = 0; a < D; ++a) off += ((bc[a] << g.lT[a]) + lc[a]) * (int)g.Kstride[a];
@@ -280,29 +299,51 @@ k_gridding_reduce(const float2* __restrict__ tiles, const int32_t* __restrict__ 
     acc[k] = make_float2(0.f, 0.f);
   }
   const int64_t pc = g.padded_cells;
+  int idx = 0;  // running index over the (e, chunk) pairs
   for (int e = 0; e < (1 << D); ++e) {
-    const int q1 = s_q1[e];
+    const int q0 = s_q0[e], q1 = s_q1[e];
     const int delta = s_delta[e];
-    for (int q = s_q0[e]; q < q1; ++q) {
+    // first pair of this e that belongs to group h
+    int q = q0 + ((h - idx) % NG + NG) % NG;
+    for (; q < q1; q += NG) {
       const float2* src = tiles + (int64_t)q * pc + delta;
 #pragma unroll
       for (int k = 0; k < CPT; ++k)
         if ((emask[k] >> e) & 1u) acc[k] = cadd(acc[k], __ldg(&src[loc0[k]]));
     }
+    idx += q1 - q0;
   }
+  if (NG > 1) {
 #pragma unroll
-  for (int k = 0; k < CPT; ++k)
-    if ((int)(threadIdx.x + k * blockDim.x) < tile_cells) grid[goff[k]] = acc[k];
+    for (int k = 0; k < CPT; ++k) part[h * (CPT * gsize) + k * gsize + tg] = acc[k];
+    __syncthreads();
+    if (h == 0) {
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) {
+        float2 t = part[k * gsize + tg];
+        for (int hh = 1; hh < NG; ++hh) t = cadd(t, part[hh * (CPT * gsize) + k * gsize + tg]);
+        acc[k] = t;
+      }
+    }
+  }
+  if (h == 0) {
+#pragma unroll
+    for (int k = 0; k < CPT; ++k)
+      if (tg + k * gsize < tile_cells) grid[goff[k]] = acc[k];
+  }
 }
 
-// The reduction gives every thread 4 cells of the tile (tile cells / 4 threads).
+// The reduction gives every thread 4 cells of the tile; small tiles get up to 4
+// thread groups, each summing every 4th (neighbour, chunk) pair.
 template <int D>
 cudaError_t launch_reduce(const nufft_plan_t* p, const float2* tiles, float2* grid) {
   int cells = 1;
   for (int a = 0; a < D; ++a) cells *= p->g.T[a];
-  const int threads = std::max(32, std::min(1024, cells / 4));
-  if ((int64_t)threads * 4 < cells) return cudaErrorInvalidValue;
-  k_gridding_reduce<D, 4><<<(unsigned)p->g.nbins, threads, 0, p->stream>>>(tiles, p->bin_chunk, grid, p->g);
+  const int gsize = std::max(32, std::min(1024, cells / 4));
+  if ((int64_t)gsize * 4 < cells) return cudaErrorInvalidValue;
+  const int NG = std::max(1, std::min(4, 1024 / gsize));   // groups splitting the chunk list
+  const size_t smem = NG > 1 ? (size_t)NG * 4 * gsize * sizeof(float2) : 0;
+  k_gridding_reduce<D, 4><<<(unsigned)p->g.nbins, gsize * NG, smem, p->stream>>>(tiles, p->bin_chunk, grid, p->g, NG);
   return cudaGetLastError();
 }
 
