@@ -1,0 +1,80 @@
+"""FP64 oracle for the paper's remaining reconstruction methods.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+* density compensation (Section 2.2.1, Eqs. 5-6): the Pipe-Menon iteration
+  w <- w / (A A^H w) and the gridding reconstruction x = A^H (y . w);
+* the paper's own two-step CG (Section 2.2.2, Eqs. 7-9): solve
+  V^H V k = V^H y for the oversampled k-space k by CG, then
+  x = S^{-1} F^{-1} k (normalised inverse FFT, crop, divide by s);
+* multi-coil operators (Section 2.2.3, Eqs. 32-33): A_i x = A (c_i . x),
+  A_multi^H A_multi x = sum_i conj(c_i) . A^H A (c_i . x), and CG on the
+  multi-coil normal equation.
+
+Readings (the paper leaves these open):
+* A A^H w is complex for real w (the Dirichlet kernel of a centred grid
+  carries a half-sample phase); the update divides by its magnitude,
+  w <- w / |A A^H w|, which keeps w real and positive.  w starts at 1.
+* F^{-1} is the normalised inverse DFT (1/K^d), S^{-1} divides by s after the
+  crop back to N^d; CG starts from k = 0.
+* coil maps c_i are complex images of the image's shape; multi-coil k-space
+  data are the coils' M-vectors stacked in coil order.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .nufft import (Plan, forward, adjoint, selfadjoint, interp_V, gridding_VH, _pad_indices, _scaling_nd)
+from .solvers import cg_solve
+
+
+# ---------------------------------------------------------------- density compensation
+def density_compensation(plan: Plan, iters: int, w0=None) -> np.ndarray:
+    """Pipe-Menon iteration (Eq. 5): w_{i+1} = w_i / |A A^H w_i|."""
+    w = np.ones(plan.M) if w0 is None else np.array(w0, dtype=np.float64)
+    for _ in range(iters):
+        d = forward(plan, adjoint(plan, w.astype(np.complex128)))
+        w = w / np.abs(d)
+    return w
+
+
+def gridding_recon(plan: Plan, y: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """Density-compensated gridding reconstruction (Eq. 6): x = A^H (y . w)."""
+    return adjoint(plan, np.asarray(y, dtype=np.complex128) * np.asarray(w, dtype=np.float64))
+
+
+# ---------------------------------------------------------------- two-step k-space CG
+def VHV(plan: Plan, k: np.ndarray) -> np.ndarray:
+    """The interpolation-gridding operator V^H V on the oversampled grid."""
+    return gridding_VH(plan, interp_V(plan, k))
+
+
+def cg_kspace(plan: Plan, y: np.ndarray, iters: int) -> np.ndarray:
+    """Eqs. 7-9: k from CG on V^H V k = V^H y, then x = S^{-1} F^{-1} k."""
+    b = gridding_VH(plan, np.asarray(y, dtype=np.complex128))
+    k = cg_solve(lambda v: VHV(plan, v), b, np.zeros(plan.Kd, dtype=np.complex128), iters)
+    z = np.fft.ifftn(k)                                   # normalised inverse DFT
+    return z[np.ix_(*_pad_indices(plan))] / _scaling_nd(plan)
+
+
+# ---------------------------------------------------------------- multi-coil
+def forward_multicoil(plan: Plan, coils: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """Stacked coil data: [A (c_0 . x); A (c_1 . x); ...] (Eq. 32's A_i)."""
+    return np.concatenate([forward(plan, c * x) for c in coils])
+
+
+def adjoint_multicoil(plan: Plan, coils: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """sum_i conj(c_i) . A^H y_i, the adjoint of forward_multicoil."""
+    M = plan.M
+    return sum(np.conj(c) * adjoint(plan, y[i * M:(i + 1) * M]) for i, c in enumerate(coils))
+
+
+def selfadjoint_multicoil(plan: Plan, coils: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """Eq. 33: sum_i conj(c_i) . A^H A (c_i . x)."""
+    return sum(np.conj(c) * selfadjoint(plan, c * x) for c in coils)
+
+
+def cg_multicoil(plan: Plan, coils: np.ndarray, y: np.ndarray, x0: np.ndarray, iters: int) -> np.ndarray:
+    """CG on the multi-coil normal equation A_multi^H A_multi x = A_multi^H y."""
+    b = adjoint_multicoil(plan, coils, y)
+    return cg_solve(lambda v: selfadjoint_multicoil(plan, coils, v), b, x0, iters)

@@ -26,6 +26,7 @@ import numpy as np
 SEED_IMAGE = 1
 SEED_TRAJ = 2
 SEED_NOISE = 3
+SEED_COILS = 4
 
 GOLDEN_ANGLE_DEG = 111.2461
 
@@ -125,6 +126,26 @@ def complex_noise(M: int, sigma: float, seed: int = SEED_NOISE) -> np.ndarray:
     """i.i.d. N(0, sigma^2) on real and imaginary parts."""
     rng = np.random.default_rng(seed)
     return (sigma * (rng.standard_normal(M) + 1j * rng.standard_normal(M))).astype(np.complex64)
+
+
+def coil_maps(nc: int, Nd, seed: int = SEED_COILS) -> np.ndarray:
+    """nc smooth complex coil sensitivities of image shape Nd (complex64):
+    Gaussian windows (sigma = N/3) centred on a circle (2D; on a ring in the
+    first two axes in 3D) with a random linear phase per coil."""
+    rng = np.random.default_rng(seed)
+    Nd = tuple(int(v) for v in Nd)
+    grids = np.meshgrid(*[np.arange(N, dtype=np.float64) - N / 2 for N in Nd], indexing="ij")
+    maps = np.empty((nc,) + Nd, dtype=np.complex64)
+    R = 0.4 * min(Nd[:2])
+    for i in range(nc):
+        ang = 2 * math.pi * i / nc
+        centre = [R * math.cos(ang), R * math.sin(ang)] + [0.0] * (len(Nd) - 2)
+        r2 = sum((g - c) ** 2 for g, c in zip(grids, centre))
+        sigma = min(Nd[:2]) / 3.0
+        slope = rng.uniform(-0.05, 0.05, size=len(Nd))
+        phase = sum(sl * g for sl, g in zip(slope, grids)) + rng.uniform(0, 2 * math.pi)
+        maps[i] = (np.exp(-r2 / (2 * sigma * sigma)) * np.exp(1j * phase)).astype(np.complex64)
+    return maps
 
 
 # ---- the named workloads -------------------------------------------------------
