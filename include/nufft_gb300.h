@@ -210,6 +210,49 @@ int solve_l1tv_ols(nufft_plan_t* plan, const float* y_dev, float* x_dev, int max
 int solve_l1tv_lad(nufft_plan_t* plan, const float* y_dev, float* x_dev, int maxiter,
                    int inner, int cg_iters, double mu, double lambda);
 
+/*
+ * nufft_density_compensation - sampling density compensation by the
+ * Pipe-Menon iteration (Section 2.2.1, Eq. 5): iters times
+ *   w <- w / |A A^H w|
+ * (A A^H w is complex for real w; its magnitude is used, keeping w real and
+ * positive).  w_dev: M float32 weights, in: the starting weights (usually all
+ * 1), out: the result.  A point whose |A A^H w| is 0 keeps its weight.  On
+ * radial trajectories the iteration with the exact operator improves for a
+ * few steps and then oscillates; a handful of iterations is the intended use.
+ */
+int nufft_density_compensation(nufft_plan_t* plan, float* w_dev, int iters);
+
+/* x = A^H (y . w), the density-compensated gridding reconstruction
+ * (Section 2.2.1, Eq. 6).  y_dev: M complex64, w_dev: M float32, x_dev: image. */
+int nufft_gridding_recon(nufft_plan_t* plan, const float* y_dev, const float* w_dev, float* x_dev);
+
+/*
+ * solve_cg_kspace - the paper's two-step least squares (Section 2.2.2,
+ * Eqs. 7-9): CG (maxiter iterations, from k = 0) on the oversampled k-space
+ * normal equation V^H V k = V^H y, then x = S^{-1} F^{-1} k (normalised
+ * inverse FFT, crop to N^d, divide by the scaling factors).  x_dev: output
+ * image.  Allocates five grid-sized work vectors on first use.
+ */
+int solve_cg_kspace(nufft_plan_t* plan, const float* y_dev, float* x_dev, int maxiter);
+
+/*
+ * Multi-coil operators (Section 2.2.3, Eqs. 32-33) for nc coil maps c_i
+ * (coils_dev: nc images, complex64, coil-major), with k-space data stacked
+ * coil by coil (nc x M complex64):
+ *   nufft_forward_multicoil      y_i = A (c_i . x)
+ *   nufft_adjoint_multicoil      x = sum_i conj(c_i) . A^H y_i
+ *   nufft_selfadjoint_multicoil  out = sum_i conj(c_i) . A^H A (c_i . x)
+ *   solve_cg_multicoil           CG on A_multi^H A_multi x = A_multi^H y
+ *                                (x_dev in: x0, out: result)
+ * nc >= 1.  Image-sized work space is allocated on first use.
+ */
+int nufft_forward_multicoil(nufft_plan_t* plan, const float* coils_dev, int nc, const float* x_dev, float* y_dev);
+int nufft_adjoint_multicoil(nufft_plan_t* plan, const float* coils_dev, int nc, const float* y_dev, float* x_dev);
+int nufft_selfadjoint_multicoil(nufft_plan_t* plan, const float* coils_dev, int nc, const float* x_dev,
+                                float* out_dev);
+int solve_cg_multicoil(nufft_plan_t* plan, const float* coils_dev, int nc, const float* y_dev, float* x_dev,
+                       int maxiter);
+
 #ifdef __cplusplus
 }
 #endif

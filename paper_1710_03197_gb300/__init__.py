@@ -30,6 +30,13 @@ from .plan import (
     solve_cg,
     solve_l1tv_ols,
     solve_l1tv_lad,
+    nufft_density_compensation,
+    nufft_gridding_recon,
+    solve_cg_kspace,
+    nufft_forward_multicoil,
+    nufft_adjoint_multicoil,
+    nufft_selfadjoint_multicoil,
+    solve_cg_multicoil,
 )
 
 __all__ = [
@@ -37,4 +44,6 @@ __all__ = [
     "nufft_plan", "nufft_forward", "nufft_adjoint", "nufft_selfadjoint",
     "nufft_forward_host", "nufft_adjoint_host", "nufft_scale_pad_fft", "nufft_interp",
     "nufft_gridding", "nufft_gridding_static", "nufft_ifft_crop_rescale", "solve_cg", "solve_l1tv_ols", "solve_l1tv_lad",
+    "nufft_density_compensation", "nufft_gridding_recon", "solve_cg_kspace", "nufft_forward_multicoil",
+    "nufft_adjoint_multicoil", "nufft_selfadjoint_multicoil", "solve_cg_multicoil",
 ]

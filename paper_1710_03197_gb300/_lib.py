@@ -53,6 +53,13 @@ _SIGS = {
     "solve_cg": (_i, [_PLAN, _vp, _vp, _i]),
     "solve_l1tv_ols": (_i, [_PLAN, _vp, _vp, _i, _i, _i, _d, _d]),
     "solve_l1tv_lad": (_i, [_PLAN, _vp, _vp, _i, _i, _i, _d, _d]),
+    "nufft_density_compensation": (_i, [_PLAN, _vp, _i]),
+    "nufft_gridding_recon": (_i, [_PLAN, _vp, _vp, _vp]),
+    "solve_cg_kspace": (_i, [_PLAN, _vp, _vp, _i]),
+    "nufft_forward_multicoil": (_i, [_PLAN, _vp, _i, _vp, _vp]),
+    "nufft_adjoint_multicoil": (_i, [_PLAN, _vp, _i, _vp, _vp]),
+    "nufft_selfadjoint_multicoil": (_i, [_PLAN, _vp, _i, _vp, _vp]),
+    "solve_cg_multicoil": (_i, [_PLAN, _vp, _i, _vp, _vp, _i]),
 }
 
 for _name, (_res, _args) in _SIGS.items():

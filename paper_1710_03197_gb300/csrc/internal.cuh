@@ -85,6 +85,10 @@ struct nufft_plan {
   // solver work space (allocated on first solver call)
   void* solver_ws;
   int64_t solver_ws_bytes;
+  // k-space CG work space (grid-sized vectors) and an M-sized buffer,
+  // allocated on first use by the calls that need them
+  void* kspace_ws;
+  float2* mbuf;
 
   char err[512];
 };

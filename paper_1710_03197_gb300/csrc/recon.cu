@@ -1,0 +1,191 @@
+// recon.cu - density compensation and multi-coil operators.
+//
+// Section 2.2.1 (Eqs. 5-6): sampling density compensation by the Pipe-Menon
+// iteration w <- w / (A A^H w) and the gridding reconstruction
+// x = A^H (y . w).  A A^H w is complex for real w (the centred grid gives the
+// point-spread function a half-sample phase); the update divides by its
+// magnitude, which keeps w real and positive.
+// Section 2.2.3 (Eqs. 32-33): multi-coil operators A_i x = A (c_i . x) and
+// A_multi^H A_multi x = sum_i conj(c_i) . A^H A (c_i . x).  The coil products
+// are elementwise kernels around the single-coil operator kernels.
+#include <initializer_list>
+#include <utility>
+
+#include "internal.cuh"
+
+namespace nufft {
+int forward_dev(nufft_plan_t* p, const float2* x, float2* y);
+int adjoint_dev(nufft_plan_t* p, const float2* y, float2* x);
+int selfadjoint_impl(nufft_plan_t* p, const float2* x, float2* out);
+
+namespace {
+
+constexpr int kThreads = 256;
+
+int blocks_for(int64_t n) {
+  int64_t b = (n + kThreads - 1) / kThreads;
+  if (b > 152 * 16) b = 152 * 16;
+  return (int)(b < 1 ? 1 : b);
+}
+
+__global__ void k_real_to_complex(const float* w, float2* out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = make_float2(w[i], 0.f);
+}
+
+// w <- w / |d|  (a point whose |d| is 0 keeps its weight)
+__global__ void k_dcf_update(float* w, const float2* d, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = d[i];
+    const float mag = sqrtf(v.x * v.x + v.y * v.y);
+    if (mag > 0.f) w[i] = w[i] / mag;
+  }
+}
+
+__global__ void k_weight(const float2* y, const float* w, float2* out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = cscale(y[i], w[i]);
+}
+
+// out = c . x
+__global__ void k_coil_mul(const float2* c, const float2* x, float2* out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = cmul(c[i], x[i]);
+}
+
+// out = conj(c) . v (first coil) or out += conj(c) . v
+__global__ void k_coil_conj_acc(const float2* c, const float2* v, float2* out, int64_t n, int first) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 t = cmulc(c[i], v[i]);
+    out[i] = first ? t : cadd(out[i], t);
+  }
+}
+
+#define TRY(x)                       \
+  do {                               \
+    int _rc = (x);                   \
+    if (_rc != NUFFT_OK) return _rc; \
+  } while (0)
+
+}  // namespace
+
+// Auxiliary buffers: two M-sized and two image-sized complex vectors.
+int get_aux(nufft_plan_t* p, float2** m0, float2** m1, float2** i0, float2** i1) {
+  const int64_t M = p->M > 0 ? p->M : 1;
+  if (!p->mbuf) {
+    const int64_t count = 2 * M + 2 * p->Nprod;
+    cudaError_t e = cudaMalloc((void**)&p->mbuf, count * sizeof(float2));
+    if (e != cudaSuccess) {
+      p->mbuf = nullptr;
+      return cuda_check(p, e, "auxiliary work space");
+    }
+    p->device_bytes += count * (int64_t)sizeof(float2);
+  }
+  *m0 = p->mbuf;
+  *m1 = p->mbuf + M;
+  *i0 = p->mbuf + 2 * M;
+  *i1 = p->mbuf + 2 * M + p->Nprod;
+  return NUFFT_OK;
+}
+
+int selfadjoint_multicoil_impl(nufft_plan_t* p, const float2* coils, int nc, const float2* x, float2* out) {
+  float2 *m0, *m1, *i0, *i1;
+  TRY(get_aux(p, &m0, &m1, &i0, &i1));
+  const int64_t n = p->Nprod;
+  for (int c = 0; c < nc; ++c) {
+    const float2* ci = coils + (int64_t)c * n;
+    k_coil_mul<<<blocks_for(n), kThreads, 0, p->stream>>>(ci, x, i0, n);
+    NUFFT_CUDA_TRY(p, cudaGetLastError());
+    TRY(selfadjoint_impl(p, i0, i1));
+    k_coil_conj_acc<<<blocks_for(n), kThreads, 0, p->stream>>>(ci, i1, out, n, c == 0);
+    NUFFT_CUDA_TRY(p, cudaGetLastError());
+  }
+  return NUFFT_OK;
+}
+
+int adjoint_multicoil_impl(nufft_plan_t* p, const float2* coils, int nc, const float2* y, float2* x) {
+  float2 *m0, *m1, *i0, *i1;
+  TRY(get_aux(p, &m0, &m1, &i0, &i1));
+  const int64_t n = p->Nprod;
+  for (int c = 0; c < nc; ++c) {
+    TRY(adjoint_dev(p, y + (int64_t)c * p->M, i0));
+    k_coil_conj_acc<<<blocks_for(n), kThreads, 0, p->stream>>>(coils + (int64_t)c * n, i0, x, n, c == 0);
+    NUFFT_CUDA_TRY(p, cudaGetLastError());
+  }
+  return NUFFT_OK;
+}
+
+}  // namespace nufft
+
+using namespace nufft;
+
+namespace {
+int check_plan_ptrs(nufft_plan_t* p, std::initializer_list<std::pair<const void*, int64_t>> ptrs) {
+  if (!p) return set_error(nullptr, NUFFT_EINVAL, "plan is NULL");
+  for (auto& pr : ptrs)
+    if (pr.second > 0 && !pr.first) return set_error(p, NUFFT_EINVAL, "a required buffer is NULL");
+  return NUFFT_OK;
+}
+}  // namespace
+
+extern "C" int nufft_density_compensation(nufft_plan_t* p, float* w_dev, int iters) {
+  TRY(check_plan_ptrs(p, {{w_dev, p ? p->M : 0}}));
+  if (iters < 0) return set_error(p, NUFFT_EINVAL, "iters < 0");
+  if (p->M == 0) return NUFFT_OK;
+  float2 *m0, *m1, *i0, *i1;
+  TRY(get_aux(p, &m0, &m1, &i0, &i1));
+  for (int it = 0; it < iters; ++it) {
+    k_real_to_complex<<<blocks_for(p->M), kThreads, 0, p->stream>>>(w_dev, m0, p->M);
+    NUFFT_CUDA_TRY(p, cudaGetLastError());
+    TRY(adjoint_dev(p, m0, i0));
+    TRY(forward_dev(p, i0, m1));
+    k_dcf_update<<<blocks_for(p->M), kThreads, 0, p->stream>>>(w_dev, m1, p->M);
+    NUFFT_CUDA_TRY(p, cudaGetLastError());
+  }
+  return NUFFT_OK;
+}
+
+extern "C" int nufft_gridding_recon(nufft_plan_t* p, const float* y_dev, const float* w_dev, float* x_dev) {
+  TRY(check_plan_ptrs(p, {{y_dev, p ? p->M : 0}, {w_dev, p ? p->M : 0}, {x_dev, p ? p->Nprod : 0}}));
+  float2 *m0, *m1, *i0, *i1;
+  TRY(get_aux(p, &m0, &m1, &i0, &i1));
+  if (p->M > 0) {
+    k_weight<<<blocks_for(p->M), kThreads, 0, p->stream>>>(reinterpret_cast<const float2*>(y_dev), w_dev, m0, p->M);
+    NUFFT_CUDA_TRY(p, cudaGetLastError());
+  }
+  return adjoint_dev(p, m0, reinterpret_cast<float2*>(x_dev));
+}
+
+extern "C" int nufft_forward_multicoil(nufft_plan_t* p, const float* coils_dev, int nc, const float* x_dev,
+                                       float* y_dev) {
+  TRY(check_plan_ptrs(p, {{coils_dev, p ? p->Nprod : 0}, {x_dev, p ? p->Nprod : 0}, {y_dev, p ? p->M : 0}}));
+  if (nc < 1) return set_error(p, NUFFT_EINVAL, "nc < 1");
+  float2 *m0, *m1, *i0, *i1;
+  TRY(get_aux(p, &m0, &m1, &i0, &i1));
+  const int64_t n = p->Nprod;
+  const float2* coils = reinterpret_cast<const float2*>(coils_dev);
+  for (int c = 0; c < nc; ++c) {
+    k_coil_mul<<<blocks_for(n), kThreads, 0, p->stream>>>(coils + (int64_t)c * n, reinterpret_cast<const float2*>(x_dev),
+                                                          i0, n);
+    NUFFT_CUDA_TRY(p, cudaGetLastError());
+    TRY(forward_dev(p, i0, reinterpret_cast<float2*>(y_dev) + (int64_t)c * p->M));
+  }
+  return NUFFT_OK;
+}
+
+extern "C" int nufft_adjoint_multicoil(nufft_plan_t* p, const float* coils_dev, int nc, const float* y_dev,
+                                       float* x_dev) {
+  TRY(check_plan_ptrs(p, {{coils_dev, p ? p->Nprod : 0}, {y_dev, p ? p->M : 0}, {x_dev, p ? p->Nprod : 0}}));
+  if (nc < 1) return set_error(p, NUFFT_EINVAL, "nc < 1");
+  return adjoint_multicoil_impl(p, reinterpret_cast<const float2*>(coils_dev), nc,
+                                reinterpret_cast<const float2*>(y_dev), reinterpret_cast<float2*>(x_dev));
+}
+
+extern "C" int nufft_selfadjoint_multicoil(nufft_plan_t* p, const float* coils_dev, int nc, const float* x_dev,
+                                           float* out_dev) {
+  TRY(check_plan_ptrs(p, {{coils_dev, p ? p->Nprod : 0}, {x_dev, p ? p->Nprod : 0}, {out_dev, p ? p->Nprod : 0}}));
+  if (nc < 1) return set_error(p, NUFFT_EINVAL, "nc < 1");
+  if ((const void*)x_dev == (const void*)out_dev) return set_error(p, NUFFT_EINVAL, "x_dev and out_dev alias");
+  return selfadjoint_multicoil_impl(p, reinterpret_cast<const float2*>(coils_dev), nc,
+                                    reinterpret_cast<const float2*>(x_dev), reinterpret_cast<float2*>(out_dev));
+}

@@ -1,8 +1,10 @@
 // solvers.cu - CG, L1TV-OLS and L1TV-LAD on the NUFFT normal operator.
 //
 // Section 2.1.5 (normal equation A^H A x = A^H y, Eq. 4), Section 2.2.2 (CG,
-// Eqs. 7-9), Section 2.2.3 (image gradient by rolling, Eq. 10; L1TV-OLS,
-// Eqs. 11-20; L1TV-LAD, Eqs. 21-31).  Bulk arithmetic is FP32; the inner
+// Eqs. 7-9, both the image-domain form and the paper's own k-space form
+// V^H V k = V^H y followed by x = S^{-1} F^{-1} k), Section 2.2.3 (image
+// gradient by rolling, Eq. 10; L1TV-OLS, Eqs. 11-20; L1TV-LAD, Eqs. 21-31;
+// multi-coil normal operator, Eqs. 32-33).  Bulk arithmetic is FP32; the inner
 // products that set the CG step lengths are accumulated in FP64 in a fixed
 // order (per-thread strided sums, a fixed shared-memory tree per CTA, then one
 // CTA summing the per-CTA results), so a solve is reproducible for a given
@@ -15,6 +17,8 @@
 namespace nufft {
 int selfadjoint_impl(nufft_plan_t* p, const float2* x, float2* out);
 int adjoint_dev(nufft_plan_t* p, const float2* y, float2* x);
+int selfadjoint_multicoil_impl(nufft_plan_t* p, const float2* coils, int nc, const float2* x, float2* out);
+int adjoint_multicoil_impl(nufft_plan_t* p, const float2* coils, int nc, const float2* y, float2* x);
 }  // namespace nufft
 
 using namespace nufft;
@@ -28,7 +32,8 @@ constexpr int kEwThreads = 256;
 // scalar slots in device memory
 enum { S_RR0 = 0, S_RR1 = 1, S_PQ = 2, S_NSLOTS = 8 };
 
-enum { V_B = 0, V_R, V_P, V_Q, V_AHY, V_AHYK, V_RHS, V_T, V_DF, V_BF, V_D0, V_B0 = V_D0 + 3, V_COUNT = V_B0 + 3 };
+enum { V_B = 0, V_R, V_P, V_Q, V_AHY, V_AHYK, V_RHS, V_T, V_DF, V_BF, V_C1, V_C2, V_D0, V_B0 = V_D0 + 3,
+       V_COUNT = V_B0 + 3 };
 
 struct Ws {
   float2* v[V_COUNT];
@@ -234,6 +239,24 @@ __global__ void k_outer(float2* ahyk, const float2* ahy, const float2* ahax, int
   }
 }
 
+#define TRY(x)                       \
+  do {                               \
+    int _rc = (x);                   \
+    if (_rc != NUFFT_OK) return _rc; \
+  } while (0)
+#define LAUNCH_CHECK(p, what) NUFFT_CUDA_TRY(p, cudaGetLastError())
+
+// x[n] /= (K^d s[n]^2): turns S crop(F^H k) into S^{-1} crop(F^{-1} k)
+__global__ void k_kspace_finish(float2* x, ImgGeom G, const float* s0, const float* s1, const float* s2,
+                                float inv_kprod) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < G.n; i += (int64_t)gridDim.x * blockDim.x) {
+    float sv = 1.f;
+    const float* sp[3] = {s0, s1, s2};
+    for (int a = 0; a < G.d; ++a) sv *= sp[a][(i / G.stride[a]) % G.N[a]];
+    x[i] = cscale(x[i], inv_kprod / (sv * sv));
+  }
+}
+
 int ew_blocks(int64_t n) {
   int64_t b = (n + kEwThreads - 1) / kEwThreads;
   if (b > 152 * 16) b = 152 * 16;
@@ -255,12 +278,31 @@ ImgGeom img_geom(const nufft_plan_t* p) {
   return G;
 }
 
-#define TRY(x)                       \
-  do {                               \
-    int _rc = (x);                   \
-    if (_rc != NUFFT_OK) return _rc; \
-  } while (0)
-#define LAUNCH_CHECK(p, what) NUFFT_CUDA_TRY(p, cudaGetLastError())
+
+
+// CG iterations on op x = b from the current x (in place), vectors of length n.
+// r, pv, q are work vectors of length n; op(in, out) applies the operator.
+template <class Op>
+int cg_core(nufft_plan_t* p, int64_t n, float2* r, float2* pv, float2* q, double* part, double* sc, Op op,
+            const float2* b, float2* x, int iters) {
+  cudaStream_t st = p->stream;
+  TRY(op(x, q));
+  k_cg_init<<<kDotBlocks, kDotThreads, 0, st>>>(r, pv, b, q, n, part);
+  k_dot_final<<<1, kDotThreads, 0, st>>>(part, sc + S_RR0);
+  LAUNCH_CHECK(p, "cg init");
+  for (int it = 0; it < iters; ++it) {
+    const int cur = (it & 1) ? S_RR1 : S_RR0;
+    const int nxt = (it & 1) ? S_RR0 : S_RR1;
+    TRY(op(pv, q));
+    k_dot_partial<<<kDotBlocks, kDotThreads, 0, st>>>(pv, q, n, part);
+    k_dot_final<<<1, kDotThreads, 0, st>>>(part, sc + S_PQ);
+    k_cg_xr<<<kDotBlocks, kDotThreads, 0, st>>>(x, r, pv, q, n, sc, cur, part);
+    k_dot_final<<<1, kDotThreads, 0, st>>>(part, sc + nxt);
+    k_cg_p<<<ew_blocks(n), kEwThreads, 0, st>>>(pv, r, n, sc, nxt, cur);
+    LAUNCH_CHECK(p, "cg iteration");
+  }
+  return NUFFT_OK;
+}
 
 struct Operator {
   bool tv;       // false: A^H A; true: K = mu A^H A + lambda sum grad^T grad
@@ -276,27 +318,11 @@ int apply_op(nufft_plan_t* p, const Operator& op, const float2* in, float2* out,
   return NUFFT_OK;
 }
 
-// cg_iters CG steps on op x = b from the current x (in place).
+// cg_iters CG steps on op x = b from the current x (in place), image-sized.
 int cg_run(nufft_plan_t* p, const Ws& w, const Operator& op, const float2* b, float2* x, int iters) {
-  const int64_t n = p->Nprod;
-  cudaStream_t st = p->stream;
-  float2 *r = w.v[V_R], *pv = w.v[V_P], *q = w.v[V_Q], *t = w.v[V_T];
-  TRY(apply_op(p, op, x, q, t));
-  k_cg_init<<<kDotBlocks, kDotThreads, 0, st>>>(r, pv, b, q, n, w.part);
-  k_dot_final<<<1, kDotThreads, 0, st>>>(w.part, w.sc + S_RR0);
-  LAUNCH_CHECK(p, "cg init");
-  for (int it = 0; it < iters; ++it) {
-    const int cur = (it & 1) ? S_RR1 : S_RR0;
-    const int nxt = (it & 1) ? S_RR0 : S_RR1;
-    TRY(apply_op(p, op, pv, q, t));
-    k_dot_partial<<<kDotBlocks, kDotThreads, 0, st>>>(pv, q, n, w.part);
-    k_dot_final<<<1, kDotThreads, 0, st>>>(w.part, w.sc + S_PQ);
-    k_cg_xr<<<kDotBlocks, kDotThreads, 0, st>>>(x, r, pv, q, n, w.sc, cur, w.part);
-    k_dot_final<<<1, kDotThreads, 0, st>>>(w.part, w.sc + nxt);
-    k_cg_p<<<ew_blocks(n), kEwThreads, 0, st>>>(pv, r, n, w.sc, nxt, cur);
-    LAUNCH_CHECK(p, "cg iteration");
-  }
-  return NUFFT_OK;
+  float2* t = w.v[V_T];
+  return cg_core(p, p->Nprod, w.v[V_R], w.v[V_P], w.v[V_Q], w.part, w.sc,
+                 [&](const float2* in, float2* out) { return apply_op(p, op, in, out, t); }, b, x, iters);
 }
 
 int check_common(nufft_plan_t* p, const float* y, const float* x) {
@@ -378,4 +404,53 @@ extern "C" int solve_l1tv_lad(nufft_plan_t* p, const float* y_dev, float* x_dev,
   TRY(check_common(p, y_dev, x_dev));
   return l1tv(p, reinterpret_cast<const float2*>(y_dev), reinterpret_cast<float2*>(x_dev), maxiter, inner, cg_iters,
               mu, lambda, true);
+}
+
+// ------------------------------------------------------------------ k-space CG (Eqs. 7-9)
+extern "C" int solve_cg_kspace(nufft_plan_t* p, const float* y_dev, float* x_dev, int maxiter) {
+  TRY(check_common(p, y_dev, x_dev));
+  if (maxiter < 0) return set_error(p, NUFFT_EINVAL, "maxiter < 0");
+  Ws w;
+  TRY(get_ws(p, &w));
+  const int64_t n = p->Kprod;
+  const int64_t vb = ((n * (int64_t)sizeof(float2) + 255) / 256) * 256;
+  if (!p->kspace_ws) {
+    cudaError_t e = cudaMalloc(&p->kspace_ws, 5 * vb);
+    if (e != cudaSuccess) { p->kspace_ws = nullptr; return cuda_check(p, e, "k-space CG work space"); }
+    p->device_bytes += 5 * vb;
+  }
+  char* base = (char*)p->kspace_ws;
+  float2 *b = (float2*)base, *r = (float2*)(base + vb), *pv = (float2*)(base + 2 * vb),
+         *q = (float2*)(base + 3 * vb), *k = (float2*)(base + 4 * vb);
+  cudaStream_t st = p->stream;
+  TRY(launch_gridding(p, reinterpret_cast<const float2*>(y_dev), b));          // V^H y
+  NUFFT_CUDA_TRY(p, cudaMemsetAsync(k, 0, n * sizeof(float2), st));
+  auto vhv = [&](const float2* in, float2* out) -> int {                       // V^H V
+    TRY(launch_interp(p, in, p->ytmp));
+    return launch_gridding(p, p->ytmp, out);
+  };
+  TRY(cg_core(p, n, r, pv, q, w.part, w.sc, vhv, b, k, maxiter));
+  TRY(launch_fft_inverse(p, k, reinterpret_cast<float2*>(x_dev)));          // S crop(F^H k)
+  const ImgGeom G = img_geom(p);
+  const float* s1 = p->g.d > 1 ? p->s + p->s_off[1] : p->s;
+  const float* s2 = p->g.d > 2 ? p->s + p->s_off[2] : p->s;
+  k_kspace_finish<<<ew_blocks(G.n), kEwThreads, 0, st>>>(reinterpret_cast<float2*>(x_dev), G, p->s + p->s_off[0], s1,
+                                                        s2, (float)(1.0 / (double)p->Kprod));
+  LAUNCH_CHECK(p, "k-space finish");
+  return NUFFT_OK;
+}
+
+// ------------------------------------------------------------------ multi-coil CG (Eqs. 32-33)
+extern "C" int solve_cg_multicoil(nufft_plan_t* p, const float* coils_dev, int nc, const float* y_dev, float* x_dev,
+                                  int maxiter) {
+  TRY(check_common(p, y_dev, x_dev));
+  if (!coils_dev || nc < 1) return set_error(p, NUFFT_EINVAL, "coils_dev is NULL or nc < 1");
+  if (maxiter < 0) return set_error(p, NUFFT_EINVAL, "maxiter < 0");
+  Ws w;
+  TRY(get_ws(p, &w));
+  const float2* coils = reinterpret_cast<const float2*>(coils_dev);
+  TRY(adjoint_multicoil_impl(p, coils, nc, reinterpret_cast<const float2*>(y_dev), w.v[V_B]));
+  auto op = [&](const float2* in, float2* out) -> int { return selfadjoint_multicoil_impl(p, coils, nc, in, out); };
+  return cg_core(p, p->Nprod, w.v[V_R], w.v[V_P], w.v[V_Q], w.part, w.sc, op, w.v[V_B],
+                 reinterpret_cast<float2*>(x_dev), maxiter);
 }

@@ -229,6 +229,68 @@ class NufftPlan:
         return x
 
 
+    # ---------------------------------------------------------------- density compensation, k-space CG
+    def density_compensation(self, iters: int, w=None):
+        """Pipe-Menon weights (Eq. 5); w: float32 CUDA tensor of M starting weights (default ones)."""
+        w = torch.ones(self.M, dtype=torch.float32, device=self.device) if w is None else w
+        self._sync_stream()
+        check(lib.nufft_density_compensation(self._h, _dev_ptr(w, self.M, "w", dtype=torch.float32), int(iters)),
+              self._h)
+        return w
+
+    def gridding_recon(self, y, w, x=None):
+        x = torch.empty(self.Nd, dtype=torch.complex64, device=self.device) if x is None else x
+        self._sync_stream()
+        check(lib.nufft_gridding_recon(self._h, _dev_ptr(y, self.M, "y"), _dev_ptr(w, self.M, "w", dtype=torch.float32),
+                                       _dev_ptr(x, self.Nprod, "x")), self._h)
+        return x
+
+    def solve_cg_kspace(self, y, x=None, maxiter=20):
+        x = torch.empty(self.Nd, dtype=torch.complex64, device=self.device) if x is None else x
+        self._sync_stream()
+        check(lib.solve_cg_kspace(self._h, _dev_ptr(y, self.M, "y"), _dev_ptr(x, self.Nprod, "x"), int(maxiter)),
+              self._h)
+        return x
+
+    # ---------------------------------------------------------------- multi-coil
+    def _coils(self, coils):
+        if coils.dim() != self.d + 1 or tuple(coils.shape[1:]) != self.Nd:
+            raise ValueError("coils must have shape (nc, *Nd)")
+        return _dev_ptr(coils, coils.shape[0] * self.Nprod, "coils"), int(coils.shape[0])
+
+    def forward_multicoil(self, coils, x, y=None):
+        cp, nc = self._coils(coils)
+        y = torch.empty(nc * self.M, dtype=torch.complex64, device=self.device) if y is None else y
+        self._sync_stream()
+        check(lib.nufft_forward_multicoil(self._h, cp, nc, _dev_ptr(x, self.Nprod, "x"), _dev_ptr(y, nc * self.M, "y")),
+              self._h)
+        return y
+
+    def adjoint_multicoil(self, coils, y, x=None):
+        cp, nc = self._coils(coils)
+        x = torch.empty(self.Nd, dtype=torch.complex64, device=self.device) if x is None else x
+        self._sync_stream()
+        check(lib.nufft_adjoint_multicoil(self._h, cp, nc, _dev_ptr(y, nc * self.M, "y"), _dev_ptr(x, self.Nprod, "x")),
+              self._h)
+        return x
+
+    def selfadjoint_multicoil(self, coils, x, out=None):
+        cp, nc = self._coils(coils)
+        out = torch.empty(self.Nd, dtype=torch.complex64, device=self.device) if out is None else out
+        self._sync_stream()
+        check(lib.nufft_selfadjoint_multicoil(self._h, cp, nc, _dev_ptr(x, self.Nprod, "x"),
+                                              _dev_ptr(out, self.Nprod, "out")), self._h)
+        return out
+
+    def solve_cg_multicoil(self, coils, y, x=None, maxiter=20):
+        cp, nc = self._coils(coils)
+        x = torch.zeros(self.Nd, dtype=torch.complex64, device=self.device) if x is None else x
+        self._sync_stream()
+        check(lib.solve_cg_multicoil(self._h, cp, nc, _dev_ptr(y, nc * self.M, "y"), _dev_ptr(x, self.Nprod, "x"),
+                                     int(maxiter)), self._h)
+        return x
+
+
 # ---------------------------------------------------------------- same names as the C ABI
 def nufft_plan(om, Nd, Kd, Jd, stream=None) -> NufftPlan:
     return NufftPlan(om, Nd, Kd, Jd, stream)
@@ -284,3 +346,31 @@ def solve_l1tv_ols(plan: NufftPlan, y, x=None, maxiter=50, inner=2, cg_iters=5, 
 
 def solve_l1tv_lad(plan: NufftPlan, y, x=None, maxiter=50, inner=2, cg_iters=5, mu=1.0, lam=0.01):
     return plan.solve_l1tv_lad(y, x, maxiter, inner, cg_iters, mu, lam)
+
+
+def nufft_density_compensation(plan: NufftPlan, iters: int, w=None):
+    return plan.density_compensation(iters, w)
+
+
+def nufft_gridding_recon(plan: NufftPlan, y, w, x=None):
+    return plan.gridding_recon(y, w, x)
+
+
+def solve_cg_kspace(plan: NufftPlan, y, x=None, maxiter=20):
+    return plan.solve_cg_kspace(y, x, maxiter)
+
+
+def nufft_forward_multicoil(plan: NufftPlan, coils, x, y=None):
+    return plan.forward_multicoil(coils, x, y)
+
+
+def nufft_adjoint_multicoil(plan: NufftPlan, coils, y, x=None):
+    return plan.adjoint_multicoil(coils, y, x)
+
+
+def nufft_selfadjoint_multicoil(plan: NufftPlan, coils, x, out=None):
+    return plan.selfadjoint_multicoil(coils, x, out)
+
+
+def solve_cg_multicoil(plan: NufftPlan, coils, y, x=None, maxiter=20):
+    return plan.solve_cg_multicoil(coils, y, x, maxiter)

@@ -1,0 +1,143 @@
+"""GPU vs oracle for density compensation (Eqs. 5-6), the paper's k-space CG
+(Eqs. 7-9) and the multi-coil operators and CG (Eqs. 32-33), through the C ABI.
+
+Tolerances: 2e-5 relative L2 for operators, 1e-4 after solver iterations
+where the iteration is stable to FP32 rounding (checked on the oracle:
+density compensation and multi-coil CG move by ~2e-6 under 1e-6 operator
+noise, the k-space CG by ~1e-6 at 10 iterations on the overdetermined case).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from oracle import extensions as X
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_OP = 2e-5
+TOL_SOLVER = 1e-4
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def nf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1710_03197_gb300 as nf
+    return nf
+
+
+def rel(a, b):
+    a, b = np.asarray(a).ravel(), np.asarray(b).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def cn(shape, seed):
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _cartesian_om(N):
+    k = 2 * math.pi * (np.arange(N) - N // 2) / N
+    g0, g1 = np.meshgrid(k, k, indexing="ij")
+    return np.stack([g0.ravel(), g1.ravel()], 1).astype(np.float32)
+
+
+@pytest.mark.parametrize("traj,iters", [("cartesian", 1), ("cartesian", 3), ("radial", 1), ("radial", 3),
+                                        ("radial", 5)])
+def test_density_compensation_matches_oracle(nf, traj, iters):
+    if traj == "cartesian":
+        om, Nd, Kd = _cartesian_om(16), (16, 16), (32, 32)
+    else:
+        om, Nd, Kd = W.radial2d_uniform(32, 64), (32, 32), (64, 64)
+    ref = oracle.make_plan(om, Nd, Kd, (6, 6))
+    with nf.NufftPlan(dev(om), Nd, Kd, (6, 6)) as plan:
+        w = host(plan.density_compensation(iters))
+    assert rel(w, X.density_compensation(ref, iters)) < TOL_SOLVER
+
+
+def test_gridding_recon_matches_oracle(nf):
+    om = W.radial2d_golden(60, 128)
+    Nd, Kd = (64, 64), (128, 128)
+    ref = oracle.make_plan(om, Nd, Kd, (6, 6))
+    y = cn(om.shape[0], 3)
+    w = np.abs(cn(om.shape[0], 4)).astype(np.float32)
+    with nf.NufftPlan(dev(om), Nd, Kd, (6, 6)) as plan:
+        x = host(plan.gridding_recon(dev(y), dev(w)))
+    assert rel(x, X.gridding_recon(ref, y, w)) < TOL_OP
+
+
+def _overdetermined():
+    Nd, Kd = (8, 8), (16, 16)
+    om = W.uniform_random_om(600, 2, seed=9)
+    ref = oracle.make_plan(om, Nd, Kd, (6, 6))
+    xt = cn(Nd, 5)
+    return Nd, Kd, om, ref, xt, oracle.forward(ref, xt).astype(np.complex64)
+
+
+def test_kspace_cg_matches_oracle(nf):
+    Nd, Kd, om, ref, xt, y = _overdetermined()
+    with nf.NufftPlan(dev(om), Nd, Kd, (6, 6)) as plan:
+        x = host(plan.solve_cg_kspace(dev(y), maxiter=10))
+    assert rel(x, X.cg_kspace(ref, y, 10)) < TOL_SOLVER
+
+
+def test_kspace_cg_recovers_the_image(nf):
+    """Consistent, overdetermined data: many iterations return x itself."""
+    Nd, Kd, om, ref, xt, y = _overdetermined()
+    with nf.NufftPlan(dev(om), Nd, Kd, (6, 6)) as plan:
+        x = host(plan.solve_cg_kspace(dev(y), maxiter=400))
+    assert rel(x, xt) < 5e-3
+
+
+def _multicoil_case(nc=4):
+    Nd, Kd = (32, 32), (64, 64)
+    om = W.uniform_random_om(1500, 2, seed=6)
+    ref = oracle.make_plan(om, Nd, Kd, (6, 6))
+    coils = W.coil_maps(nc, Nd)
+    return Nd, Kd, om, ref, coils
+
+
+def test_multicoil_operators_match_oracle(nf):
+    Nd, Kd, om, ref, coils = _multicoil_case()
+    x = cn(Nd, 6)
+    y = cn(4 * om.shape[0], 7)
+    with nf.NufftPlan(dev(om), Nd, Kd, (6, 6)) as plan:
+        cd = dev(coils)
+        yf = host(plan.forward_multicoil(cd, dev(x)))
+        xa = host(plan.adjoint_multicoil(cd, dev(y)))
+        xs = host(plan.selfadjoint_multicoil(cd, dev(x)))
+    c128 = coils.astype(np.complex128)
+    assert rel(yf, X.forward_multicoil(ref, c128, x)) < TOL_OP
+    assert rel(xa, X.adjoint_multicoil(ref, c128, y)) < TOL_OP
+    assert rel(xs, X.selfadjoint_multicoil(ref, c128, x)) < TOL_OP
+
+
+def test_multicoil_cg_matches_oracle(nf):
+    Nd, Kd, om, ref, coils = _multicoil_case()
+    c128 = coils.astype(np.complex128)
+    y = X.forward_multicoil(ref, c128, W.complex_normal_image(Nd)).astype(np.complex64)
+    with nf.NufftPlan(dev(om), Nd, Kd, (6, 6)) as plan:
+        x = host(plan.solve_cg_multicoil(dev(coils), dev(y), maxiter=20))
+    assert rel(x, X.cg_multicoil(ref, c128, y, np.zeros(Nd), 20)) < TOL_SOLVER
+
+
+def test_multicoil_rejects_bad_coil_shape(nf):
+    Nd, Kd, om, ref, coils = _multicoil_case()
+    with nf.NufftPlan(dev(om), Nd, Kd, (6, 6)) as plan:
+        with pytest.raises(ValueError):
+            plan.forward_multicoil(dev(coils[:, :16]), dev(cn(Nd, 1)))
+        assert nf.lib.nufft_forward_multicoil(plan.handle, None, 4, None, None) == 1     # EINVAL
