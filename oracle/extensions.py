@@ -78,3 +78,58 @@ def cg_multicoil(plan: Plan, coils: np.ndarray, y: np.ndarray, x0: np.ndarray, i
     """CG on the multi-coil normal equation A_multi^H A_multi x = A_multi^H y."""
     b = adjoint_multicoil(plan, coils, y)
     return cg_solve(lambda v: selfadjoint_multicoil(plan, coils, v), b, x0, iters)
+
+
+# ---------------------------------------------------------------- trajectory derivative
+def _dr_domega(om_1d: np.ndarray, k0: np.ndarray, s: np.ndarray, K: int, J: int) -> np.ndarray:
+    """d r_j / d w = sum_n s_n (-i t_n) exp(-i (w - gamma (k0 + j)) t_n), shape (M, J)."""
+    from .minmax import centred_coords
+    t = centred_coords(s.shape[0])
+    gamma = (2.0 * np.pi) / K
+    M = om_1d.shape[0]
+    dr = np.empty((M, J), dtype=np.complex128)
+    for j in range(1, J + 1):
+        u = om_1d - gamma * (k0 + j)
+        E = np.exp(-1j * u[:, None] * t[None, :])
+        dr[:, j - 1] = E @ (s * (-1j) * t)
+    return dr
+
+
+def coefficient_derivatives(plan: Plan) -> list:
+    """Per dimension, d c / d w (M, J): the min-max coefficients c = G^{-1} r
+    with G independent of w and the neighbourhood k0 held fixed, so
+    dc/dw = G^{-1} dr/dw.  (k0 jumps at cell boundaries, where the interpolator
+    is discontinuous; the derivative is the one-sided one inside a cell.)"""
+    from .minmax import minmax_G
+    out = []
+    for dim in range(plan.d):
+        K, J = plan.Kd[dim], plan.Jd[dim]
+        G = minmax_G(plan.s[dim], K, J)
+        dr = _dr_domega(plan.om[:, dim], plan.k0[:, dim], plan.s[dim], K, J)
+        out.append(np.linalg.solve(G, dr.T).T)
+    return out
+
+
+def forward_domega(plan: Plan, x: np.ndarray) -> np.ndarray:
+    """d y_m / d w_{m,a} for every point and dimension, shape (M, d)."""
+    import itertools
+    from .nufft import scale_pad, fft_forward
+    Y = fft_forward(scale_pad(plan, x))
+    dc = coefficient_derivatives(plan)
+    out = np.zeros((plan.M, plan.d), dtype=np.complex128)
+    for taps in itertools.product(*[range(1, J + 1) for J in plan.Jd]):
+        idx = tuple((plan.k0[:, dim] + taps[dim]) % plan.Kd[dim] for dim in range(plan.d))
+        v = Y[idx]
+        for a in range(plan.d):
+            w = np.ones(plan.M, dtype=np.complex128)
+            for dim in range(plan.d):
+                w = w * (dc[dim][:, taps[dim] - 1] if dim == a else plan.coef[dim][:, taps[dim] - 1])
+            out[:, a] += w * v
+    return out
+
+
+def trajectory_gradient(plan: Plan, x: np.ndarray, g: np.ndarray) -> np.ndarray:
+    """Gradient of a real loss L(y), y = A(w) x, with respect to w (M, d), given
+    g = dL/dRe(y) + i dL/dIm(y): dL/dw_{m,a} = Re(conj(g_m) dy_m/dw_{m,a})."""
+    dy = forward_domega(plan, x)
+    return np.real(np.conj(np.asarray(g, dtype=np.complex128))[:, None] * dy)

@@ -115,3 +115,56 @@ def test_coil_maps_are_smooth_and_distinct():
     # neighbouring pixels differ little (smooth), different coils peak in different places
     assert np.abs(np.diff(np.abs(c), axis=-1)).max() < 0.1
     assert len(set(int(np.argmax(m)) for m in mags)) == 8
+
+
+def _fd_case():
+    Nd, Kd, Jd = (16, 16), (32, 32), (6, 6)
+    om = W.uniform_random_om(200, 2, seed=12).astype(np.float64)
+    x = W.complex_normal_image(Nd).astype(complex)
+    return Nd, Kd, Jd, om, x
+
+
+def test_trajectory_derivative_matches_central_differences():
+    """FP64 central differences, step 1e-6, on points away from cell boundaries
+    (the neighbourhood jumps there and the interpolator is discontinuous)."""
+    Nd, Kd, Jd, om, x = _fd_case()
+    p = oracle.make_plan(om, Nd, Kd, Jd)
+    dy = X.forward_domega(p, x)
+    h = 1e-6
+    u = om / (2 * math.pi / Kd[0])
+    away = (np.abs(u - np.round(u)) > 1e-3).all(1)
+    for a in range(2):
+        op, omn = om.copy(), om.copy()
+        op[:, a] += h
+        omn[:, a] -= h
+        fd = (oracle.forward(oracle.make_plan(op, Nd, Kd, Jd), x) -
+              oracle.forward(oracle.make_plan(omn, Nd, Kd, Jd), x)) / (2 * h)
+        assert _rel(dy[away, a], fd[away]) < 1e-7
+
+
+def test_trajectory_derivative_approximates_the_exact_nudft_derivative():
+    Nd, Kd, Jd, om, x = _fd_case()
+    p = oracle.make_plan(om, Nd, Kd, Jd)
+    dy = X.forward_domega(p, x)
+    t = np.arange(16) - 8
+    T0, T1 = np.meshgrid(t, t, indexing="ij")
+    E = np.exp(-1j * (om[:, :1] * T0.ravel()[None] + om[:, 1:] * T1.ravel()[None]))
+    for a, Ta in enumerate((T0, T1)):
+        exact = (E * (-1j * Ta.ravel()[None])) @ x.ravel()
+        assert _rel(dy[:, a], exact) < 1e-4
+
+
+def test_trajectory_gradient_of_a_quadratic_loss():
+    """L = ||A(w) x - y0||^2 has dL/dw = Re(conj(2 (A x - y0)) dy/dw); checked by FD on L."""
+    Nd, Kd, Jd, om, x = _fd_case()
+    y0 = _cn(om.shape[0])
+    p = oracle.make_plan(om, Nd, Kd, Jd)
+    r = oracle.forward(p, x) - y0
+    g = X.trajectory_gradient(p, x, 2 * r)
+    h = 1e-6
+    m, a = 17, 1
+    op, omn = om.copy(), om.copy()
+    op[m, a] += h
+    omn[m, a] -= h
+    L = lambda o: np.sum(np.abs(oracle.forward(oracle.make_plan(o, Nd, Kd, Jd), x) - y0) ** 2)
+    assert abs((L(op) - L(omn)) / (2 * h) - g[m, a]) < 1e-6 * abs(g[m, a]) + 1e-8
