@@ -253,6 +253,22 @@ int nufft_selfadjoint_multicoil(nufft_plan_t* plan, const float* coils_dev, int 
 int solve_cg_multicoil(nufft_plan_t* plan, const float* coils_dev, int nc, const float* y_dev, float* x_dev,
                        int maxiter);
 
+/*
+ * nufft_trajectory_gradient - gradient of a real loss L(y), y = A(om) x, with
+ * respect to the trajectory (the forward operator of Section 2.1, Eq. 1,
+ * differentiated through the min-max coefficients of Section 2.1.3; the paper
+ * itself has no derivative):
+ *   gom[m, a] = Re(conj(g_m) d y_m / d om[m, a]),  g = dL/dRe(y) + i dL/dIm(y),
+ * with d c / d om = G^{-1} d r / d om and the neighbourhood held fixed (the
+ * interpolator is discontinuous where a point crosses a grid-cell boundary).
+ *   x_dev    image the forward operator was applied to
+ *   g_dev    M complex64
+ *   gom_dev  M x d float32, row-major, trajectory order
+ * The derivative coefficients are computed (FP64, stored complex64) on the
+ * first call and kept by the plan.  The image gradient is nufft_adjoint(g).
+ */
+int nufft_trajectory_gradient(nufft_plan_t* plan, const float* x_dev, const float* g_dev, float* gom_dev);
+
 #ifdef __cplusplus
 }
 #endif

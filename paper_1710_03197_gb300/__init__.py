@@ -37,7 +37,9 @@ from .plan import (
     nufft_adjoint_multicoil,
     nufft_selfadjoint_multicoil,
     solve_cg_multicoil,
+    nufft_trajectory_gradient,
 )
+from .autograd import NufftFunction, nufft_apply
 
 __all__ = [
     "lib", "LIB_PATH", "NufftError", "check", "symbols_declared", "NufftPlan",
@@ -46,4 +48,5 @@ __all__ = [
     "nufft_gridding", "nufft_gridding_static", "nufft_ifft_crop_rescale", "solve_cg", "solve_l1tv_ols", "solve_l1tv_lad",
     "nufft_density_compensation", "nufft_gridding_recon", "solve_cg_kspace", "nufft_forward_multicoil",
     "nufft_adjoint_multicoil", "nufft_selfadjoint_multicoil", "solve_cg_multicoil",
+    "nufft_trajectory_gradient", "NufftFunction", "nufft_apply",
 ]

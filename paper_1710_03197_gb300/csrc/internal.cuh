@@ -90,6 +90,13 @@ struct nufft_plan {
   void* kspace_ws;
   float2* mbuf;
 
+  // kept from plan creation for the trajectory derivative
+  double* s64;              // scaling in FP64, dim i at s_off[i]
+  double2* Tinv;            // J_i x J_i min-max inverses, dim i at T_off[i]
+  int64_t T_off[nufft::kMaxDim];
+  float* om_sorted;         // [d][M] trajectory in tile-sorted order
+  float2* dcoef;            // [sum_i J_i][M] d coef / d omega (allocated on first use)
+
   char err[512];
 };
 
@@ -115,6 +122,8 @@ int launch_gridding(nufft_plan_t* p, const float2* y, float2* grid);
 
 // Plan-time helpers (plan.cu).
 Points points_view(const nufft_plan_t* p);
+// d coef / d omega into p->dcoef (allocated here on first use).
+int ensure_coef_derivatives(nufft_plan_t* p);
 
 }  // namespace nufft
 

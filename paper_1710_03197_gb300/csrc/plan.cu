@@ -282,16 +282,22 @@ __global__ void k_bin_start(const uint32_t* key, int64_t M, int64_t nbins, int32
 }
 
 // Per sorted point and dimension: first neighbour and the J min-max coefficients.
-__global__ void k_coefficients(const float* om, Geom g, int64_t M, const int32_t* perm, const double* s64,
-                               DimTables D, const double2* Tinv, int32_t* kf_out, float2* coef,
-                               int64_t coef_off0, int64_t coef_off1, int64_t coef_off2) {
+// With deriv = 1 the same kernel writes d c / d w = T d r / d w instead, where
+// d r_j / d w = sum_n s_n (-i t_n) exp(-i theta t_n) (the neighbourhood fixed):
+// the summand gains the factor -i t_n.  om_sorted = 1: om is [d][M] in sorted
+// order; otherwise om is the caller's M x d array and perm maps to it, and the
+// sorted copy is written to om_out (if not NULL).
+__global__ void k_coefficients(const float* om, int om_sorted, Geom g, int64_t M, const int32_t* perm,
+                               const double* s64, DimTables D, const double2* Tinv, int32_t* kf_out, float2* coef,
+                               int64_t coef_off0, int64_t coef_off1, int64_t coef_off2, int deriv, float* om_out) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= M * g.d) return;
   const int a = (int)(idx / M);
   const int64_t i = idx - (int64_t)a * M;
-  const int64_t m = perm[i];
   const int N = g.N[a], K = g.K[a], J = g.J[a];
-  const double w = (double)om[m * g.d + a];
+  const float wf = om_sorted ? om[(int64_t)a * M + i] : om[(int64_t)perm[i] * g.d + a];
+  if (om_out) om_out[(int64_t)a * M + i] = wf;
+  const double w = (double)wf;
   const double k0 = offset_k0(w, K, J);
   const double gamma = (2.0 * kPi) / K;
   const double* s = s64 + D.s_off[a];
@@ -306,8 +312,14 @@ __global__ void k_coefficients(const float* om, Geom g, int64_t M, const int32_t
     sincos(theta * 0.5 * N, &es, &ec);   // value at n = 0 (t = -N/2)
     double re = 0.0, im = 0.0;
     for (int n = 0; n < N; ++n) {
-      re += s[n] * ec;
-      im += s[n] * es;
+      if (deriv) {              // s_n (-i t_n) e_n = s_n t_n (es - i ec)
+        const double st = s[n] * ((double)n - 0.5 * N);
+        re += st * es;
+        im -= st * ec;
+      } else {
+        re += s[n] * ec;
+        im += s[n] * es;
+      }
       const double nc = ec * cs - es * sn;
       const double ns = ec * sn + es * cs;
       ec = nc;
@@ -326,7 +338,7 @@ __global__ void k_coefficients(const float* om, Geom g, int64_t M, const int32_t
     }
     coef[off + (int64_t)j * M + i] = make_float2((float)re, (float)im);
   }
-  kf_out[(int64_t)a * M + i] = wrap_first(k0, K);
+  if (kf_out) kf_out[(int64_t)a * M + i] = wrap_first(k0, K);
 }
 
 // Order each chunk's points for the gridding kernel.  Lane groups of J_last
@@ -410,7 +422,8 @@ cudaError_t dalloc(nufft_plan_t* p, T** ptr, int64_t count) {
 
 void free_plan_memory(nufft_plan_t* p) {
   void* bufs[] = {p->s, p->twiddle, p->kf, p->coef, p->perm, p->bin_start, p->chunks, p->bin_chunk,
-                  p->tiles, p->grid, p->ytmp, p->x_stage, p->y_stage, p->solver_ws, p->kspace_ws, p->mbuf};
+                  p->tiles, p->grid, p->ytmp, p->x_stage, p->y_stage, p->solver_ws, p->kspace_ws, p->mbuf,
+                  p->s64, p->Tinv, p->om_sorted, p->dcoef};
   for (void* b : bufs)
     if (b) cudaFree(b);
 }
@@ -449,14 +462,14 @@ int build_plan(nufft_plan_t* p, const float* om) {
     p->s_off[a] = s_tot; p->tw_off[a] = tw_tot;
     s_tot += g.N[a]; tw_tot += g.K[a]; T_tot += (int64_t)g.J[a] * g.J[a];
   }
-  double* s64 = nullptr;
-  double2* Tinv = nullptr;
   NUFFT_CUDA_TRY(p, dalloc(p, &p->s, s_tot));
   NUFFT_CUDA_TRY(p, dalloc(p, &p->twiddle, tw_tot));
-  NUFFT_CUDA_TRY(p, cudaMalloc((void**)&s64, s_tot * sizeof(double)));
-  struct Tmp { void* a; void* b; void* c; void* d; void* e; ~Tmp() { for (void* v : {a, b, c, d, e}) if (v) cudaFree(v); } } tmp{s64, nullptr, nullptr, nullptr, nullptr};
-  NUFFT_CUDA_TRY(p, cudaMalloc((void**)&Tinv, T_tot * sizeof(double2)));
-  tmp.b = Tinv;
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->s64, s_tot));
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->Tinv, T_tot));
+  for (int a = 0; a < d; ++a) p->T_off[a] = D.T_off[a];
+  double* s64 = p->s64;
+  double2* Tinv = p->Tinv;
+  struct Tmp { void* a; void* b; void* c; void* d; void* e; ~Tmp() { for (void* v : {a, b, c, d, e}) if (v) cudaFree(v); } } tmp{nullptr, nullptr, nullptr, nullptr, nullptr};
   k_scaling_twiddle<<<d, 256, 0, st>>>(D, p->s, s64, p->twiddle);
   NUFFT_CUDA_TRY(p, cudaGetLastError());
   k_minmax_T<<<d, 256, 0, st>>>(D, s64, Tinv, flag + 1);
@@ -543,10 +556,12 @@ int build_plan(nufft_plan_t* p, const float* om) {
   for (int a = 0; a < d; ++a) { p->coef_off[a] = coef_tot; coef_tot += (int64_t)g.J[a] * M; }
   NUFFT_CUDA_TRY(p, dalloc(p, &p->kf, M * d));
   NUFFT_CUDA_TRY(p, dalloc(p, &p->coef, coef_tot));
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->om_sorted, M * d));
   if (M > 0) {
     const int64_t n = M * d;
-    k_coefficients<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(om, g, M, p->perm, s64, D, Tinv, p->kf, p->coef,
-                                                               p->coef_off[0], p->coef_off[1], p->coef_off[2]);
+    k_coefficients<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(om, 0, g, M, p->perm, s64, D, Tinv, p->kf, p->coef,
+                                                               p->coef_off[0], p->coef_off[1], p->coef_off[2], 0,
+                                                               p->om_sorted);
     NUFFT_CUDA_TRY(p, cudaGetLastError());
   }
   NUFFT_CUDA_TRY(p, cudaMemcpyAsync(hflag, flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -564,6 +579,27 @@ int build_plan(nufft_plan_t* p, const float* om) {
 }
 
 }  // namespace
+
+int ensure_coef_derivatives(nufft_plan_t* p) {
+  if (p->dcoef || p->M == 0) return NUFFT_OK;
+  int64_t tot = 0;
+  for (int a = 0; a < p->g.d; ++a) tot += (int64_t)p->g.J[a] * p->M;
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->dcoef, tot));
+  DimTables D;
+  memset(&D, 0, sizeof(D));
+  D.d = p->g.d;
+  for (int a = 0; a < p->g.d; ++a) {
+    D.N[a] = p->g.N[a]; D.K[a] = p->g.K[a]; D.J[a] = p->g.J[a];
+    D.s_off[a] = p->s_off[a]; D.tw_off[a] = p->tw_off[a]; D.T_off[a] = p->T_off[a];
+  }
+  const int64_t n = p->M * p->g.d;
+  k_coefficients<<<(unsigned)((n + 127) / 128), 128, 0, p->stream>>>(
+      p->om_sorted, 1, p->g, p->M, p->perm, p->s64, D, p->Tinv, nullptr, p->dcoef, p->coef_off[0], p->coef_off[1],
+      p->coef_off[2], 1, nullptr);
+  NUFFT_CUDA_TRY(p, cudaGetLastError());
+  return NUFFT_OK;
+}
+
 }  // namespace nufft
 
 using namespace nufft;

@@ -229,6 +229,15 @@ class NufftPlan:
         return x
 
 
+    # ---------------------------------------------------------------- trajectory gradient
+    def trajectory_gradient(self, x, g, gom=None):
+        """Re(conj(g) dy/dom) as an (M, d) float32 tensor (C: nufft_trajectory_gradient)."""
+        gom = torch.empty((self.M, self.d), dtype=torch.float32, device=self.device) if gom is None else gom
+        self._sync_stream()
+        check(lib.nufft_trajectory_gradient(self._h, _dev_ptr(x, self.Nprod, "x"), _dev_ptr(g, self.M, "g"),
+                                            _dev_ptr(gom, self.M * self.d, "gom", dtype=torch.float32)), self._h)
+        return gom
+
     # ---------------------------------------------------------------- density compensation, k-space CG
     def density_compensation(self, iters: int, w=None):
         """Pipe-Menon weights (Eq. 5); w: float32 CUDA tensor of M starting weights (default ones)."""
@@ -374,3 +383,7 @@ def nufft_selfadjoint_multicoil(plan: NufftPlan, coils, x, out=None):
 
 def solve_cg_multicoil(plan: NufftPlan, coils, y, x=None, maxiter=20):
     return plan.solve_cg_multicoil(coils, y, x, maxiter)
+
+
+def nufft_trajectory_gradient(plan: NufftPlan, x, g, gom=None):
+    return plan.trajectory_gradient(x, g, gom)

@@ -157,6 +157,8 @@ WORKLOADS = {
     "radial2d_256": dict(d=2, Nd=(256, 256), Kd=(512, 512), Jd=(6, 6)),
     # 3D 128^3 -> 256^3, J=6, kooshball 8192 spokes x 256 samples (2,097,152 points)
     "kooshball3d_128": dict(d=3, Nd=(128, 128, 128), Kd=(256, 256, 256), Jd=(6, 6, 6)),
+    # 2D 256x256 -> 512x512, J=6, 16 spiral interleaves x 2048 samples, om + N(0, 1e-3) rad (32,768 points)
+    "spiral2d_256": dict(d=2, Nd=(256, 256), Kd=(512, 512), Jd=(6, 6)),
 }
 
 
@@ -175,6 +177,11 @@ def make_workload(name: str):
         om = kooshball3d(8192, 256)
         x = complex_normal_image(spec["Nd"])
         noise = None
+    elif name == "spiral2d_256":
+        rng = np.random.default_rng(SEED_TRAJ)
+        om = (spiral2d(16, 2048).astype(np.float64) + 1e-3 * rng.standard_normal((16 * 2048, 2))).astype(np.float32)
+        x = ellipse_phantom(256)
+        noise = complex_noise(om.shape[0], 0.1)
     else:  # pragma: no cover
         raise KeyError(name)
     spec["M"] = om.shape[0]
