@@ -303,6 +303,10 @@ def ours(args):
     with ClockSampler(torch.cuda.current_device() if world == 1 else local, clocks_path) as clk:
         results = {n: run_workload(nf, torch, n, args.steps, args.warmup, dev, flush_bytes,
                                    solvers=(i == 0 and not args.no_solvers)) for i, n in enumerate(names)}
+        next_rows = None
+        if not args.no_solvers:
+            next_rows = {"f1_multicoil_dynamic": run_multicoil_dynamic(nf, torch, dev),
+                         "f2_differentiable_spiral": run_differentiable(nf, torch, dev)}
     torch.cuda.synchronize()
     res2 = results[names[0]]
     res3 = results[names[1]] if len(names) > 1 else None
@@ -350,6 +354,7 @@ def ours(args):
         "stages": stages2,
         "monolithic_ms_per_step": round(statistics.mean(res2["mono_ms"]), 5),
         "rows": res2["rows"],
+        "next_rows": next_rows,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }
@@ -366,6 +371,103 @@ def ours(args):
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------------ next rows: batched multi-coil, differentiable
+
+def run_multicoil_dynamic(nf, torch, dev, reps: int = 5):
+    """32 coils x 8 frames, 256^2, uneven golden-angle frames: the multi-coil
+    normal operator sum_i conj(c_i) A_f^H A_f (c_i x_f) for every frame, batched
+    (one launch per stage for all coils of a frame) against the plain form
+    (one single-coil A^H A call per coil, coil products as tensor ops)."""
+    frames = W.dynamic_radial_frames(8, 512)
+    Nd, Kd, Jd = (256, 256), (512, 512), (6, 6)
+    nc = 32
+    coils = torch.from_numpy(W.coil_maps(nc, Nd)).to(dev)
+    x = torch.from_numpy(W.ellipse_phantom(256)).to(dev)
+    plans = [nf.NufftPlan(torch.from_numpy(om).to(dev), Nd, Kd, Jd) for om in frames]
+    out = torch.empty(Nd, dtype=torch.complex64, device=dev)
+    tmp = torch.empty(Nd, dtype=torch.complex64, device=dev)
+
+    def batched():
+        for p in plans:
+            p.selfadjoint_multicoil(coils, x, out)
+
+    def plain():
+        for p in plans:
+            out.zero_()
+            for c in range(nc):
+                p.selfadjoint(coils[c] * x, tmp)
+                out.add_(coils[c].conj() * tmp)
+
+    res = {}
+    for key, fn in (("batched", batched), ("plain", plain)):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        e1.synchronize()
+        res[key] = e0.elapsed_time(e1) / reps
+    samples = nc * sum(om.shape[0] for om in frames)
+    for p in plans:
+        p.close()
+    return {"workload": "32 coils x 8 frames, 256^2, golden-angle frames of U{13..89} spokes x 512 samples "
+                        f"({samples} coil samples), grid 512^2, J=6x6",
+            "batched_ms": round(res["batched"], 4), "plain_ms": round(res["plain"], 4),
+            "batched_coil_samples_per_s": round(samples / (res["batched"] * 1e-3), 1),
+            "plain_coil_samples_per_s": round(samples / (res["plain"] * 1e-3), 1)}
+
+
+def run_differentiable(nf, torch, dev, reps: int = 5):
+    """256^2 spiral (16 x 2048, om + N(0, 1e-3)): forward + backward through the
+    autograd function (plan rebuilt each step, since om is a variable) against
+    the plain forward + adjoint with a fixed plan; then 50 L1TV-LAD iterations."""
+    spec, om, x, noise = W.make_workload("spiral2d_256")
+    Nd, Kd, Jd = spec["Nd"], spec["Kd"], spec["Jd"]
+    om_d = torch.from_numpy(om).to(dev)
+    x_d = torch.from_numpy(x).to(dev)
+    plan = nf.NufftPlan(om_d, Nd, Kd, Jd)
+    y0 = (plan.forward(x_d) + torch.from_numpy(noise).to(dev)).contiguous()
+
+    def diff_step():
+        om_t = om_d.clone().requires_grad_(True)
+        x_t = x_d.clone().requires_grad_(True)
+        y = nf.nufft_apply(om_t, x_t, Nd, Kd, Jd)
+        torch.sum(torch.abs(y - y0) ** 2).backward()
+
+    def diff_step_fixed_plan():
+        om_t = om_d.clone().requires_grad_(True)
+        x_t = x_d.clone().requires_grad_(True)
+        y = nf.nufft_apply(om_t, x_t, Nd, Kd, Jd, plan)
+        torch.sum(torch.abs(y - y0) ** 2).backward()
+
+    def plain_step():
+        y = plan.forward(x_d)
+        plan.adjoint((y - y0).contiguous())
+
+    res = {}
+    for key, fn in (("autograd_with_plan_ms", diff_step), ("autograd_fixed_plan_ms", diff_step_fixed_plan),
+                    ("plain_fwd_adj_ms", plain_step)):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        res[key] = round((time.perf_counter() - t0) / reps * 1e3, 4)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    plan.solve_l1tv_lad(y0, maxiter=50, inner=2, cg_iters=5, mu=1.0, lam=0.01)
+    e1.record()
+    e1.synchronize()
+    res["l1tv_lad_50_iterations_ms"] = round(e0.elapsed_time(e1), 3)
+    res["workload"] = "256^2 ellipse phantom, 16 spiral interleaves x 2048 samples (32,768 points), grid 512^2, J=6x6"
+    res["points"] = int(om.shape[0])
+    plan.close()
+    return res
 
 
 # ------------------------------------------------------------------ oracle timing (CPU baseline / reference arm)

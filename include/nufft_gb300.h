@@ -211,6 +211,22 @@ int solve_l1tv_lad(nufft_plan_t* plan, const float* y_dev, float* x_dev, int max
                    int inner, int cg_iters, double mu, double lambda);
 
 /*
+ * Batched operators: nb independent transforms with one plan (one trajectory),
+ * e.g. the coil images of one frame.  x_dev: nb images back to back, y_dev:
+ * nb x M complex64 (element b at y_dev + 2 b M floats).  Each stage runs as
+ * one launch for the whole batch.  The first call with a given nb allocates
+ * (and keeps) nb-sized work space: nb grids, nb sets of gridding partial
+ * tiles, nb x M samples and nb images.  Results equal nb single calls.
+ *   nufft_forward_batch      y_b = A x_b        (Section 2.1, Eq. 1)
+ *   nufft_adjoint_batch      x_b = A^H y_b      (Section 2.1.4, Eq. 2)
+ *   nufft_selfadjoint_batch  out_b = A^H A x_b  (Section 2.1.5); x and out
+ *                            may not alias
+ */
+int nufft_forward_batch(nufft_plan_t* plan, int nb, const float* x_dev, float* y_dev);
+int nufft_adjoint_batch(nufft_plan_t* plan, int nb, const float* y_dev, float* x_dev);
+int nufft_selfadjoint_batch(nufft_plan_t* plan, int nb, const float* x_dev, float* out_dev);
+
+/*
  * nufft_density_compensation - sampling density compensation by the
  * Pipe-Menon iteration (Section 2.2.1, Eq. 5): iters times
  *   w <- w / |A A^H w|
@@ -244,7 +260,8 @@ int solve_cg_kspace(nufft_plan_t* plan, const float* y_dev, float* x_dev, int ma
  *   nufft_selfadjoint_multicoil  out = sum_i conj(c_i) . A^H A (c_i . x)
  *   solve_cg_multicoil           CG on A_multi^H A_multi x = A_multi^H y
  *                                (x_dev in: x0, out: result)
- * nc >= 1.  Image-sized work space is allocated on first use.
+ * nc >= 1.  The nc coils run as one batch (see nufft_forward_batch); the
+ * batched work space is allocated on first use with a given nc.
  */
 int nufft_forward_multicoil(nufft_plan_t* plan, const float* coils_dev, int nc, const float* x_dev, float* y_dev);
 int nufft_adjoint_multicoil(nufft_plan_t* plan, const float* coils_dev, int nc, const float* y_dev, float* x_dev);

@@ -38,6 +38,9 @@ from .plan import (
     nufft_selfadjoint_multicoil,
     solve_cg_multicoil,
     nufft_trajectory_gradient,
+    nufft_forward_batch,
+    nufft_adjoint_batch,
+    nufft_selfadjoint_batch,
 )
 from .autograd import NufftFunction, nufft_apply
 
@@ -49,4 +52,5 @@ __all__ = [
     "nufft_density_compensation", "nufft_gridding_recon", "solve_cg_kspace", "nufft_forward_multicoil",
     "nufft_adjoint_multicoil", "nufft_selfadjoint_multicoil", "solve_cg_multicoil",
     "nufft_trajectory_gradient", "NufftFunction", "nufft_apply",
+    "nufft_forward_batch", "nufft_adjoint_batch", "nufft_selfadjoint_batch",
 ]

@@ -61,6 +61,9 @@ _SIGS = {
     "nufft_selfadjoint_multicoil": (_i, [_PLAN, _vp, _i, _vp, _vp]),
     "solve_cg_multicoil": (_i, [_PLAN, _vp, _i, _vp, _vp, _i]),
     "nufft_trajectory_gradient": (_i, [_PLAN, _vp, _vp, _vp]),
+    "nufft_forward_batch": (_i, [_PLAN, _i, _vp, _vp]),
+    "nufft_adjoint_batch": (_i, [_PLAN, _i, _vp, _vp]),
+    "nufft_selfadjoint_batch": (_i, [_PLAN, _i, _vp, _vp]),
 }
 
 for _name, (_res, _args) in _SIGS.items():

@@ -45,6 +45,50 @@ int selfadjoint_impl(nufft_plan_t* p, const float2* x, float2* out) {
 }
 int forward_dev(nufft_plan_t* p, const float2* x, float2* y) { return forward_impl(p, x, y); }
 int adjoint_dev(nufft_plan_t* p, const float2* y, float2* x) { return adjoint_impl(p, y, x); }
+
+// Batched work space for nb transforms at once (grown on demand, kept).
+int ensure_batch(nufft_plan_t* p, int nb) {
+  if (nb <= p->batch_cap) return NUFFT_OK;
+  for (float2** b : {&p->bgrid, &p->btiles, &p->bytmp, &p->bimg})
+    if (*b) { cudaFree(*b); *b = nullptr; }
+  p->batch_cap = 0;
+  const int64_t counts[4] = {(int64_t)nb * p->Kprod, (int64_t)nb * p->nchunks * p->g.padded_cells,
+                             (int64_t)nb * (p->M > 0 ? p->M : 1), (int64_t)nb * p->Nprod};
+  float2** bufs[4] = {&p->bgrid, &p->btiles, &p->bytmp, &p->bimg};
+  for (int k = 0; k < 4; ++k) {
+    if (counts[k] == 0) continue;
+    cudaError_t e = cudaMalloc((void**)bufs[k], counts[k] * sizeof(float2));
+    if (e != cudaSuccess) { *bufs[k] = nullptr; return cuda_check(p, e, "batched work space"); }
+    p->device_bytes += counts[k] * (int64_t)sizeof(float2);
+  }
+  p->batch_cap = nb;
+  return NUFFT_OK;
+}
+
+// nb transforms: x is nb images, y is nb x M.
+int forward_batch_impl(nufft_plan_t* p, int nb, const float2* x, float2* y) {
+  if (nb == 1) return forward_impl(p, x, y);
+  if (p->M == 0) return NUFFT_OK;
+  TRY(ensure_batch(p, nb));
+  TRY(launch_fft_forward(p, x, p->bgrid, nb));
+  return launch_interp(p, p->bgrid, y, nb);
+}
+
+int adjoint_batch_impl(nufft_plan_t* p, int nb, const float2* y, float2* x) {
+  if (nb == 1) return adjoint_impl(p, y, x);
+  TRY(ensure_batch(p, nb));
+  TRY(launch_gridding(p, y, p->bgrid, nb, p->btiles));
+  return launch_fft_inverse(p, p->bgrid, x, nb);
+}
+
+int selfadjoint_batch_impl(nufft_plan_t* p, int nb, const float2* x, float2* out) {
+  if (nb == 1) return selfadjoint_impl(p, x, out);
+  TRY(ensure_batch(p, nb));
+  TRY(launch_fft_forward(p, x, p->bgrid, nb));
+  TRY(launch_interp(p, p->bgrid, p->bytmp, nb));
+  TRY(launch_gridding(p, p->bytmp, p->bgrid, nb, p->btiles));
+  return launch_fft_inverse(p, p->bgrid, out, nb);
+}
 }  // namespace nufft
 
 extern "C" int nufft_forward(nufft_plan_t* p, const float* x_dev, float* y_dev) {
@@ -119,4 +163,29 @@ extern "C" int nufft_ifft_crop_rescale(nufft_plan_t* p, float* grid_dev, float* 
   TRY(check_ptr(p, grid_dev, p->Kprod, "grid_dev"));
   TRY(check_ptr(p, x_dev, p->Nprod, "x_dev"));
   return launch_fft_inverse(p, reinterpret_cast<float2*>(grid_dev), reinterpret_cast<float2*>(x_dev));
+}
+
+extern "C" int nufft_forward_batch(nufft_plan_t* p, int nb, const float* x_dev, float* y_dev) {
+  TRY(check_plan(p));
+  if (nb < 1) return set_error(p, NUFFT_EINVAL, "nb < 1");
+  TRY(check_ptr(p, x_dev, p->Nprod, "x_dev"));
+  TRY(check_ptr(p, y_dev, p->M, "y_dev"));
+  return forward_batch_impl(p, nb, reinterpret_cast<const float2*>(x_dev), reinterpret_cast<float2*>(y_dev));
+}
+
+extern "C" int nufft_adjoint_batch(nufft_plan_t* p, int nb, const float* y_dev, float* x_dev) {
+  TRY(check_plan(p));
+  if (nb < 1) return set_error(p, NUFFT_EINVAL, "nb < 1");
+  TRY(check_ptr(p, y_dev, p->M, "y_dev"));
+  TRY(check_ptr(p, x_dev, p->Nprod, "x_dev"));
+  return adjoint_batch_impl(p, nb, reinterpret_cast<const float2*>(y_dev), reinterpret_cast<float2*>(x_dev));
+}
+
+extern "C" int nufft_selfadjoint_batch(nufft_plan_t* p, int nb, const float* x_dev, float* out_dev) {
+  TRY(check_plan(p));
+  if (nb < 1) return set_error(p, NUFFT_EINVAL, "nb < 1");
+  TRY(check_ptr(p, x_dev, p->Nprod, "x_dev"));
+  TRY(check_ptr(p, out_dev, p->Nprod, "out_dev"));
+  if ((const void*)x_dev == (const void*)out_dev) return set_error(p, NUFFT_EINVAL, "x_dev and out_dev alias");
+  return selfadjoint_batch_impl(p, nb, reinterpret_cast<const float2*>(x_dev), reinterpret_cast<float2*>(out_dev));
 }

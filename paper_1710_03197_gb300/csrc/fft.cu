@@ -40,6 +40,8 @@ struct FftArgs {
   int64_t inner;              // prod_{i>a} K_i (grid stride of axis a)
   int src_image;              // forward first pass: read the image, apply S
   int dst_image;              // inverse last pass: write the image, apply S^H
+  int64_t src_bstride;        // batch strides (blockIdx.y selects the batch element)
+  int64_t dst_bstride;
 };
 
 template <bool INV>
@@ -162,6 +164,8 @@ k_fft_pass(const FftArgs A, const int W) {
     in = 0;
   }
   const bool live = o < A.nouter;
+  const float2* __restrict__ src = A.src + (int64_t)blockIdx.y * A.src_bstride;
+  float2* __restrict__ dst = A.dst + (int64_t)blockIdx.y * A.dst_bstride;
 
   // Outer coordinates: image index on axes < a, mapped to padded grid positions.
   int64_t goff = 0;
@@ -190,13 +194,13 @@ k_fft_pass(const FftArgs A, const int W) {
         if (in_image) {
           if (A.src_image) {
             const int n = p < half ? p + half : p - L + half;
-            v = cscale(__ldg(&A.src[o * A.Na + n]), A.s_axis[n] * slead);
+            v = cscale(__ldg(&src[o * A.Na + n]), A.s_axis[n] * slead);
           } else {
-            v = A.src[goff + (int64_t)p * stride + in];
+            v = src[goff + (int64_t)p * stride + in];
           }
         }
       } else {
-        v = A.src[goff + (int64_t)p * stride + in];
+        v = src[goff + (int64_t)p * stride + in];
       }
     }
     sm[SI.at(b, p)] = v;
@@ -219,15 +223,15 @@ k_fft_pass(const FftArgs A, const int W) {
     const int p = t + k * TPL;
     const float2 v = sm[SI.at(b, p)];
     if (!INV) {
-      A.dst[goff + (int64_t)p * stride + in] = v;
+      dst[goff + (int64_t)p * stride + in] = v;
     } else {
       const bool in_image = (p < half) || (p >= L - half);
       if (!in_image) continue;
       if (A.dst_image) {
         const int n = p < half ? p + half : p - L + half;
-        A.dst[o * A.Na + n] = cscale(v, A.s_axis[n] * slead);
+        dst[o * A.Na + n] = cscale(v, A.s_axis[n] * slead);
       } else {
-        A.dst[goff + (int64_t)p * stride + in] = v;
+        dst[goff + (int64_t)p * stride + in] = v;
       }
     }
   }
@@ -239,7 +243,7 @@ k_fft_pass(const FftArgs A, const int W) {
 constexpr int64_t kTargetBlocks = 2 * 152;
 
 template <int L, bool STRIDED, bool INV>
-cudaError_t launch_L(const FftArgs& A, cudaStream_t st) {
+cudaError_t launch_L(const FftArgs& A, int nb, cudaStream_t st) {
   constexpr int TPL = L / 8;
   int W;
   int64_t blocks;
@@ -260,20 +264,20 @@ cudaError_t launch_L(const FftArgs& A, cudaStream_t st) {
     if (e != cudaSuccess) return e;
   }
   if (blocks == 0) return cudaSuccess;
-  k_fft_pass<L, STRIDED, INV><<<(unsigned)blocks, threads, smem, st>>>(A, W);
+  k_fft_pass<L, STRIDED, INV><<<dim3((unsigned)blocks, (unsigned)nb), threads, smem, st>>>(A, W);
   return cudaGetLastError();
 }
 
 template <bool STRIDED, bool INV>
-cudaError_t launch_any(int L, const FftArgs& A, cudaStream_t st) {
+cudaError_t launch_any(int L, const FftArgs& A, int nb, cudaStream_t st) {
   switch (L) {
-    case 16: return launch_L<16, STRIDED, INV>(A, st);
-    case 32: return launch_L<32, STRIDED, INV>(A, st);
-    case 64: return launch_L<64, STRIDED, INV>(A, st);
-    case 128: return launch_L<128, STRIDED, INV>(A, st);
-    case 256: return launch_L<256, STRIDED, INV>(A, st);
-    case 512: return launch_L<512, STRIDED, INV>(A, st);
-    case 1024: return launch_L<1024, STRIDED, INV>(A, st);
+    case 16: return launch_L<16, STRIDED, INV>(A, nb, st);
+    case 32: return launch_L<32, STRIDED, INV>(A, nb, st);
+    case 64: return launch_L<64, STRIDED, INV>(A, nb, st);
+    case 128: return launch_L<128, STRIDED, INV>(A, nb, st);
+    case 256: return launch_L<256, STRIDED, INV>(A, nb, st);
+    case 512: return launch_L<512, STRIDED, INV>(A, nb, st);
+    case 1024: return launch_L<1024, STRIDED, INV>(A, nb, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -300,31 +304,35 @@ FftArgs make_args(const nufft_plan_t* p, int a) {
 
 }  // namespace
 
-int launch_fft_forward(nufft_plan_t* p, const float2* x, float2* grid) {
+int launch_fft_forward(nufft_plan_t* p, const float2* x, float2* grid, int nb) {
   const int d = p->g.d;
   for (int a = d - 1; a >= 0; --a) {
     FftArgs A = make_args(p, a);
     A.src_image = (a == d - 1);
     A.src = A.src_image ? x : grid;
     A.dst = grid;
+    A.src_bstride = A.src_image ? p->Nprod : p->Kprod;
+    A.dst_bstride = p->Kprod;
     const bool strided = A.inner > 1;
-    cudaError_t e = strided ? launch_any<true, false>(p->g.K[a], A, p->stream)
-                            : launch_any<false, false>(p->g.K[a], A, p->stream);
+    cudaError_t e = strided ? launch_any<true, false>(p->g.K[a], A, nb, p->stream)
+                            : launch_any<false, false>(p->g.K[a], A, nb, p->stream);
     if (e != cudaSuccess) return cuda_check(p, e, "forward FFT pass");
   }
   return NUFFT_OK;
 }
 
-int launch_fft_inverse(nufft_plan_t* p, float2* grid, float2* x) {
+int launch_fft_inverse(nufft_plan_t* p, float2* grid, float2* x, int nb) {
   const int d = p->g.d;
   for (int a = 0; a < d; ++a) {
     FftArgs A = make_args(p, a);
     A.dst_image = (a == d - 1);
     A.src = grid;
     A.dst = A.dst_image ? x : grid;
+    A.src_bstride = p->Kprod;
+    A.dst_bstride = A.dst_image ? p->Nprod : p->Kprod;
     const bool strided = A.inner > 1;
-    cudaError_t e = strided ? launch_any<true, true>(p->g.K[a], A, p->stream)
-                            : launch_any<false, true>(p->g.K[a], A, p->stream);
+    cudaError_t e = strided ? launch_any<true, true>(p->g.K[a], A, nb, p->stream)
+                            : launch_any<false, true>(p->g.K[a], A, nb, p->stream);
     if (e != cudaSuccess) return cuda_check(p, e, "inverse FFT pass");
   }
   return NUFFT_OK;

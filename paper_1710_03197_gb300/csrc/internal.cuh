@@ -97,6 +97,13 @@ struct nufft_plan {
   float* om_sorted;         // [d][M] trajectory in tile-sorted order
   float2* dcoef;            // [sum_i J_i][M] d coef / d omega (allocated on first use)
 
+  // batched work space (grown on demand): grids, partial tiles, k-space, images
+  int batch_cap;
+  float2* bgrid;            // [batch_cap][Kprod]
+  float2* btiles;           // [batch_cap][nchunks][padded_cells]
+  float2* bytmp;            // [batch_cap][M]
+  float2* bimg;             // [batch_cap][Nprod]
+
   char err[512];
 };
 
@@ -113,12 +120,21 @@ int cuda_check(nufft_plan_t* p, cudaError_t e, const char* what);
 
 // ------------------------------------------------------------------ launchers
 // FFT passes (fft.cu).  Forward: grid = F pad(S x).  Inverse: x = S crop(F^H grid).
-int launch_fft_forward(nufft_plan_t* p, const float2* x, float2* grid);
-int launch_fft_inverse(nufft_plan_t* p, float2* grid, float2* x);
+// nb > 1 runs nb independent transforms: images nb x N^d, grids nb x K^d.
+int launch_fft_forward(nufft_plan_t* p, const float2* x, float2* grid, int nb = 1);
+int launch_fft_inverse(nufft_plan_t* p, float2* grid, float2* x, int nb = 1);
 
 // Interpolation and gridding (interp.cu).
-int launch_interp(nufft_plan_t* p, const float2* grid, float2* y);
-int launch_gridding(nufft_plan_t* p, const float2* y, float2* grid);
+// nb > 1: grids nb x K^d, k-space data nb x M, partial tiles in `tiles`
+// (nb x nchunks x padded tile; NULL = the plan's single-batch buffer).
+int launch_interp(nufft_plan_t* p, const float2* grid, float2* y, int nb = 1);
+int launch_gridding(nufft_plan_t* p, const float2* y, float2* grid, int nb = 1, float2* tiles = nullptr);
+
+// Batched operators (capi.cu): nb transforms with one launch per stage.
+int ensure_batch(nufft_plan_t* p, int nb);
+int forward_batch_impl(nufft_plan_t* p, int nb, const float2* x, float2* y);
+int adjoint_batch_impl(nufft_plan_t* p, int nb, const float2* y, float2* x);
+int selfadjoint_batch_impl(nufft_plan_t* p, int nb, const float2* x, float2* out);
 
 // Plan-time helpers (plan.cu).
 Points points_view(const nufft_plan_t* p);

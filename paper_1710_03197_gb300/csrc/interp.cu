@@ -31,7 +31,10 @@ namespace {
 // ---------------------------------------------------------------- interpolation
 template <int D, int JF>
 __global__ void __launch_bounds__(256)
-k_interp(const float2* __restrict__ grid, float2* __restrict__ y, const Points P, const Geom g) {
+k_interp(const float2* __restrict__ grid_b, float2* __restrict__ y_b, const Points P, const Geom g, int64_t gbs,
+         int64_t ybs) {
+  const float2* __restrict__ grid = grid_b + (int64_t)blockIdx.y * gbs;
+  float2* __restrict__ y = y_b + (int64_t)blockIdx.y * ybs;
   const int G = JF > 0 ? JF : g.J[D - 1];
   const int lane = threadIdx.x & 31;
   const int per_warp = 32 / G;
@@ -116,9 +119,11 @@ struct GridChunkCfg {
 
 template <int D, int JF>
 __global__ void __launch_bounds__(GridChunkCfg<D, JF>::kThreads, GridChunkCfg<D, JF>::kMinBlocks)
-k_gridding_chunk(const float2* __restrict__ y, float2* __restrict__ tiles, const Chunk* __restrict__ chunks,
-                 const Points P, const Geom g) {
+k_gridding_chunk(const float2* __restrict__ y_b, float2* __restrict__ tiles_b, const Chunk* __restrict__ chunks,
+                 const Points P, const Geom g, int64_t ybs, int64_t tbs) {
   extern __shared__ float sm[];
+  const float2* __restrict__ y = y_b + (int64_t)blockIdx.y * ybs;
+  float2* __restrict__ tiles = tiles_b + (int64_t)blockIdx.y * tbs;
   const int ncell = (int)g.padded_cells;
   float* sre = sm;
   float* sim = sm + ncell;
@@ -226,8 +231,10 @@ k_gridding_chunk(const float2* __restrict__ y, float2* __restrict__ tiles, const
 // source bin's chunks, in a fixed order.
 template <int D, int CPT>
 __global__ void __launch_bounds__(1024)
-k_gridding_reduce(const float2* __restrict__ tiles, const int32_t* __restrict__ bin_chunk,
-                  float2* __restrict__ grid, const Geom g, const int NG) {
+k_gridding_reduce(const float2* __restrict__ tiles_b, const int32_t* __restrict__ bin_chunk,
+                  float2* __restrict__ grid_b, const Geom g, const int NG, int64_t tbs, int64_t gbs) {
+  const float2* __restrict__ tiles = tiles_b + (int64_t)blockIdx.y * tbs;
+  float2* __restrict__ grid = grid_b + (int64_t)blockIdx.y * gbs;
   // NG thread groups of blockDim/NG threads; group h takes every NG-th (e, chunk)
   // pair, and the groups' sums are added in group order at the end.
   extern __shared__ float2 part[];
@@ -336,14 +343,15 @@ k_gridding_reduce(const float2* __restrict__ tiles, const int32_t* __restrict__ 
 // The reduction gives every thread 4 cells of the tile; small tiles get up to 4
 // thread groups, each summing every 4th (neighbour, chunk) pair.
 template <int D>
-cudaError_t launch_reduce(const nufft_plan_t* p, const float2* tiles, float2* grid) {
+cudaError_t launch_reduce(const nufft_plan_t* p, const float2* tiles, float2* grid, int nb = 1) {
   int cells = 1;
   for (int a = 0; a < D; ++a) cells *= p->g.T[a];
   const int gsize = std::max(32, std::min(1024, cells / 4));
   if ((int64_t)gsize * 4 < cells) return cudaErrorInvalidValue;
   const int NG = std::max(1, std::min(4, 1024 / gsize));   // groups splitting the chunk list
   const size_t smem = NG > 1 ? (size_t)NG * 4 * gsize * sizeof(float2) : 0;
-  k_gridding_reduce<D, 4><<<(unsigned)p->g.nbins, gsize * NG, smem, p->stream>>>(tiles, p->bin_chunk, grid, p->g, NG);
+  k_gridding_reduce<D, 4><<<dim3((unsigned)p->g.nbins, (unsigned)nb), gsize * NG, smem, p->stream>>>(
+      tiles, p->bin_chunk, grid, p->g, NG, p->nchunks * p->g.padded_cells, p->Kprod);
   return cudaGetLastError();
 }
 
@@ -354,37 +362,41 @@ bool all_j_equal(const Geom& g, int J) {
 }
 
 template <int D>
-cudaError_t interp_d(const nufft_plan_t* p, const float2* grid, float2* y) {
+cudaError_t interp_d(const nufft_plan_t* p, const float2* grid, float2* y, int nb) {
   const Points P = points_view(p);
   const int G = p->g.J[D - 1];
   const int per_warp = 32 / G;
   const int64_t warps = (P.M + per_warp - 1) / per_warp;
   const int64_t blocks = (warps * 32 + 255) / 256;
   if (blocks == 0) return cudaSuccess;
-  if (all_j_equal(p->g, 6)) k_interp<D, 6><<<(unsigned)blocks, 256, 0, p->stream>>>(grid, y, P, p->g);
-  else k_interp<D, 0><<<(unsigned)blocks, 256, 0, p->stream>>>(grid, y, P, p->g);
+  const dim3 gd((unsigned)blocks, (unsigned)nb);
+  if (all_j_equal(p->g, 6)) k_interp<D, 6><<<gd, 256, 0, p->stream>>>(grid, y, P, p->g, p->Kprod, p->M);
+  else k_interp<D, 0><<<gd, 256, 0, p->stream>>>(grid, y, P, p->g, p->Kprod, p->M);
   return cudaGetLastError();
 }
 
 template <int D>
-cudaError_t gridding_d(const nufft_plan_t* p, const float2* y, float2* grid) {
+cudaError_t gridding_d(const nufft_plan_t* p, const float2* y, float2* grid, int nb, float2* tiles) {
   const Points P = points_view(p);
+  const int64_t tbs = p->nchunks * p->g.padded_cells;
   const size_t smem = (size_t)p->g.padded_cells * sizeof(float2);
   constexpr int NT = GridChunkCfg<D, 6>::kThreads;
   if (p->nchunks > 0) {
     if (all_j_equal(p->g, 6)) {
       cudaError_t e = cudaFuncSetAttribute(k_gridding_chunk<D, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      k_gridding_chunk<D, 6><<<(unsigned)p->nchunks, NT, smem, p->stream>>>(y, p->tiles, p->chunks, P, p->g);
+      k_gridding_chunk<D, 6><<<dim3((unsigned)p->nchunks, (unsigned)nb), NT, smem, p->stream>>>(
+          y, tiles, p->chunks, P, p->g, p->M, tbs);
     } else {
       cudaError_t e = cudaFuncSetAttribute(k_gridding_chunk<D, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      k_gridding_chunk<D, 0><<<(unsigned)p->nchunks, NT, smem, p->stream>>>(y, p->tiles, p->chunks, P, p->g);
+      k_gridding_chunk<D, 0><<<dim3((unsigned)p->nchunks, (unsigned)nb), NT, smem, p->stream>>>(
+          y, tiles, p->chunks, P, p->g, p->M, tbs);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  return launch_reduce<D>(p, p->tiles, grid);
+  return launch_reduce<D>(p, tiles, grid, nb);
 }
 
 // ---------------------------------------------------------------- gridding without allocation
@@ -420,11 +432,11 @@ cudaError_t gridding_static_d(const nufft_plan_t* p, const float2* y, float2* gr
     if (all_j_equal(p->g, 6)) {
       cudaError_t e = cudaFuncSetAttribute(k_gridding_chunk<D, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      k_gridding_chunk<D, 6><<<(unsigned)p->nchunks, NT, smem, p->stream>>>(y, tiles, p->chunks, P, p->g);
+      k_gridding_chunk<D, 6><<<(unsigned)p->nchunks, NT, smem, p->stream>>>(y, tiles, p->chunks, P, p->g, 0, 0);
     } else {
       cudaError_t e = cudaFuncSetAttribute(k_gridding_chunk<D, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      k_gridding_chunk<D, 0><<<(unsigned)p->nchunks, NT, smem, p->stream>>>(y, tiles, p->chunks, P, p->g);
+      k_gridding_chunk<D, 0><<<(unsigned)p->nchunks, NT, smem, p->stream>>>(y, tiles, p->chunks, P, p->g, 0, 0);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -434,22 +446,23 @@ cudaError_t gridding_static_d(const nufft_plan_t* p, const float2* y, float2* gr
 
 }  // namespace
 
-int launch_interp(nufft_plan_t* p, const float2* grid, float2* y) {
+int launch_interp(nufft_plan_t* p, const float2* grid, float2* y, int nb) {
   cudaError_t e;
   switch (p->g.d) {
-    case 1: e = interp_d<1>(p, grid, y); break;
-    case 2: e = interp_d<2>(p, grid, y); break;
-    default: e = interp_d<3>(p, grid, y); break;
+    case 1: e = interp_d<1>(p, grid, y, nb); break;
+    case 2: e = interp_d<2>(p, grid, y, nb); break;
+    default: e = interp_d<3>(p, grid, y, nb); break;
   }
   return e == cudaSuccess ? NUFFT_OK : cuda_check(p, e, "interpolation kernel");
 }
 
-int launch_gridding(nufft_plan_t* p, const float2* y, float2* grid) {
+int launch_gridding(nufft_plan_t* p, const float2* y, float2* grid, int nb, float2* tiles) {
+  if (!tiles) tiles = p->tiles;
   cudaError_t e;
   switch (p->g.d) {
-    case 1: e = gridding_d<1>(p, y, grid); break;
-    case 2: e = gridding_d<2>(p, y, grid); break;
-    default: e = gridding_d<3>(p, y, grid); break;
+    case 1: e = gridding_d<1>(p, y, grid, nb, tiles); break;
+    case 2: e = gridding_d<2>(p, y, grid, nb, tiles); break;
+    default: e = gridding_d<3>(p, y, grid, nb, tiles); break;
   }
   return e == cudaSuccess ? NUFFT_OK : cuda_check(p, e, "gridding kernels");
 }

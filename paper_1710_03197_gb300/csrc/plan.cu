@@ -423,7 +423,7 @@ cudaError_t dalloc(nufft_plan_t* p, T** ptr, int64_t count) {
 void free_plan_memory(nufft_plan_t* p) {
   void* bufs[] = {p->s, p->twiddle, p->kf, p->coef, p->perm, p->bin_start, p->chunks, p->bin_chunk,
                   p->tiles, p->grid, p->ytmp, p->x_stage, p->y_stage, p->solver_ws, p->kspace_ws, p->mbuf,
-                  p->s64, p->Tinv, p->om_sorted, p->dcoef};
+                  p->s64, p->Tinv, p->om_sorted, p->dcoef, p->bgrid, p->btiles, p->bytmp, p->bimg};
   for (void* b : bufs)
     if (b) cudaFree(b);
 }

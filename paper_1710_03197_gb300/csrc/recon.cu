@@ -6,8 +6,9 @@
 // point-spread function a half-sample phase); the update divides by its
 // magnitude, which keeps w real and positive.
 // Section 2.2.3 (Eqs. 32-33): multi-coil operators A_i x = A (c_i . x) and
-// A_multi^H A_multi x = sum_i conj(c_i) . A^H A (c_i . x).  The coil products
-// are elementwise kernels around the single-coil operator kernels.
+// A_multi^H A_multi x = sum_i conj(c_i) . A^H A (c_i . x).  All coils run as
+// one batch of the NUFFT kernels (one launch per stage), between one kernel
+// that forms every coil image and one that sums the conjugate-weighted coils.
 #include <initializer_list>
 #include <utility>
 
@@ -53,11 +54,19 @@ __global__ void k_coil_mul(const float2* c, const float2* x, float2* out, int64_
     out[i] = cmul(c[i], x[i]);
 }
 
-// out = conj(c) . v (first coil) or out += conj(c) . v
-__global__ void k_coil_conj_acc(const float2* c, const float2* v, float2* out, int64_t n, int first) {
+// out[b] = c[b] . x for all nc coils (nc x n outputs)
+__global__ void k_coil_mul_all(const float2* c, const float2* x, float2* out, int64_t n, int nc) {
+  const int64_t tot = n * nc;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < tot; k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = cmul(c[k], x[k % n]);
+}
+
+// out = sum_b conj(c[b]) . v[b], coils summed in order b = 0..nc-1
+__global__ void k_coil_conj_reduce(const float2* c, const float2* v, float2* out, int64_t n, int nc) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const float2 t = cmulc(c[i], v[i]);
-    out[i] = first ? t : cadd(out[i], t);
+    float2 acc = make_float2(0.f, 0.f);
+    for (int b = 0; b < nc; ++b) acc = cadd(acc, cmulc(c[(int64_t)b * n + i], v[(int64_t)b * n + i]));
+    out[i] = acc;
   }
 }
 
@@ -88,30 +97,41 @@ int get_aux(nufft_plan_t* p, float2** m0, float2** m1, float2** i0, float2** i1)
   return NUFFT_OK;
 }
 
+// All coils of the operator run as one batch: one coil-multiply kernel, one
+// launch per NUFFT stage for the nc transforms, one conjugate-coil reduction.
 int selfadjoint_multicoil_impl(nufft_plan_t* p, const float2* coils, int nc, const float2* x, float2* out) {
-  float2 *m0, *m1, *i0, *i1;
-  TRY(get_aux(p, &m0, &m1, &i0, &i1));
   const int64_t n = p->Nprod;
-  for (int c = 0; c < nc; ++c) {
-    const float2* ci = coils + (int64_t)c * n;
-    k_coil_mul<<<blocks_for(n), kThreads, 0, p->stream>>>(ci, x, i0, n);
-    NUFFT_CUDA_TRY(p, cudaGetLastError());
-    TRY(selfadjoint_impl(p, i0, i1));
-    k_coil_conj_acc<<<blocks_for(n), kThreads, 0, p->stream>>>(ci, i1, out, n, c == 0);
-    NUFFT_CUDA_TRY(p, cudaGetLastError());
+  float2 *imgs, *res;      // coil images in, A^H A of each coil image out
+  if (nc == 1) {
+    float2 *m0, *m1, *i0, *i1;
+    TRY(get_aux(p, &m0, &m1, &i0, &i1));
+    imgs = i0;
+    res = i1;
+  } else {
+    TRY(ensure_batch(p, nc));
+    imgs = res = p->bimg;  // the batched operator reads its input before writing its output
   }
+  k_coil_mul_all<<<blocks_for(n * nc), kThreads, 0, p->stream>>>(coils, x, imgs, n, nc);
+  NUFFT_CUDA_TRY(p, cudaGetLastError());
+  TRY(selfadjoint_batch_impl(p, nc, imgs, res));
+  k_coil_conj_reduce<<<blocks_for(n), kThreads, 0, p->stream>>>(coils, res, out, n, nc);
+  NUFFT_CUDA_TRY(p, cudaGetLastError());
   return NUFFT_OK;
 }
 
 int adjoint_multicoil_impl(nufft_plan_t* p, const float2* coils, int nc, const float2* y, float2* x) {
-  float2 *m0, *m1, *i0, *i1;
-  TRY(get_aux(p, &m0, &m1, &i0, &i1));
-  const int64_t n = p->Nprod;
-  for (int c = 0; c < nc; ++c) {
-    TRY(adjoint_dev(p, y + (int64_t)c * p->M, i0));
-    k_coil_conj_acc<<<blocks_for(n), kThreads, 0, p->stream>>>(coils + (int64_t)c * n, i0, x, n, c == 0);
-    NUFFT_CUDA_TRY(p, cudaGetLastError());
+  float2* imgs;
+  if (nc == 1) {
+    float2 *m0, *m1, *i0, *i1;
+    TRY(get_aux(p, &m0, &m1, &i0, &i1));
+    imgs = i0;
+  } else {
+    TRY(ensure_batch(p, nc));
+    imgs = p->bimg;
   }
+  TRY(adjoint_batch_impl(p, nc, y, imgs));
+  k_coil_conj_reduce<<<blocks_for(p->Nprod), kThreads, 0, p->stream>>>(coils, imgs, x, p->Nprod, nc);
+  NUFFT_CUDA_TRY(p, cudaGetLastError());
   return NUFFT_OK;
 }
 
@@ -160,17 +180,20 @@ extern "C" int nufft_forward_multicoil(nufft_plan_t* p, const float* coils_dev, 
                                        float* y_dev) {
   TRY(check_plan_ptrs(p, {{coils_dev, p ? p->Nprod : 0}, {x_dev, p ? p->Nprod : 0}, {y_dev, p ? p->M : 0}}));
   if (nc < 1) return set_error(p, NUFFT_EINVAL, "nc < 1");
-  float2 *m0, *m1, *i0, *i1;
-  TRY(get_aux(p, &m0, &m1, &i0, &i1));
-  const int64_t n = p->Nprod;
-  const float2* coils = reinterpret_cast<const float2*>(coils_dev);
-  for (int c = 0; c < nc; ++c) {
-    k_coil_mul<<<blocks_for(n), kThreads, 0, p->stream>>>(coils + (int64_t)c * n, reinterpret_cast<const float2*>(x_dev),
-                                                          i0, n);
-    NUFFT_CUDA_TRY(p, cudaGetLastError());
-    TRY(forward_dev(p, i0, reinterpret_cast<float2*>(y_dev) + (int64_t)c * p->M));
+  float2* imgs;
+  if (nc == 1) {
+    float2 *m0, *m1, *i0, *i1;
+    TRY(get_aux(p, &m0, &m1, &i0, &i1));
+    imgs = i0;
+  } else {
+    TRY(ensure_batch(p, nc));
+    imgs = p->bimg;
   }
-  return NUFFT_OK;
+  const int64_t n = p->Nprod;
+  k_coil_mul_all<<<blocks_for(n * nc), kThreads, 0, p->stream>>>(reinterpret_cast<const float2*>(coils_dev),
+                                                                 reinterpret_cast<const float2*>(x_dev), imgs, n, nc);
+  NUFFT_CUDA_TRY(p, cudaGetLastError());
+  return forward_batch_impl(p, nc, imgs, reinterpret_cast<float2*>(y_dev));
 }
 
 extern "C" int nufft_adjoint_multicoil(nufft_plan_t* p, const float* coils_dev, int nc, const float* y_dev,

@@ -229,6 +229,37 @@ class NufftPlan:
         return x
 
 
+    # ---------------------------------------------------------------- batches (one plan, nb transforms)
+    def _batch(self, t, per, name):
+        nb = t.numel() // per
+        if nb < 1 or nb * per != t.numel():
+            raise ValueError(f"{name} must hold a whole number of elements of size {per}")
+        return nb
+
+    def forward_batch(self, x, y=None):
+        nb = self._batch(x, self.Nprod, "x")
+        y = torch.empty((nb, self.M), dtype=torch.complex64, device=self.device) if y is None else y
+        self._sync_stream()
+        check(lib.nufft_forward_batch(self._h, nb, _dev_ptr(x, nb * self.Nprod, "x"), _dev_ptr(y, nb * self.M, "y")),
+              self._h)
+        return y
+
+    def adjoint_batch(self, y, x=None):
+        nb = self._batch(y, self.M, "y")
+        x = torch.empty((nb,) + self.Nd, dtype=torch.complex64, device=self.device) if x is None else x
+        self._sync_stream()
+        check(lib.nufft_adjoint_batch(self._h, nb, _dev_ptr(y, nb * self.M, "y"), _dev_ptr(x, nb * self.Nprod, "x")),
+              self._h)
+        return x
+
+    def selfadjoint_batch(self, x, out=None):
+        nb = self._batch(x, self.Nprod, "x")
+        out = torch.empty((nb,) + self.Nd, dtype=torch.complex64, device=self.device) if out is None else out
+        self._sync_stream()
+        check(lib.nufft_selfadjoint_batch(self._h, nb, _dev_ptr(x, nb * self.Nprod, "x"),
+                                          _dev_ptr(out, nb * self.Nprod, "out")), self._h)
+        return out
+
     # ---------------------------------------------------------------- trajectory gradient
     def trajectory_gradient(self, x, g, gom=None):
         """Re(conj(g) dy/dom) as an (M, d) float32 tensor (C: nufft_trajectory_gradient)."""
@@ -387,3 +418,15 @@ def solve_cg_multicoil(plan: NufftPlan, coils, y, x=None, maxiter=20):
 
 def nufft_trajectory_gradient(plan: NufftPlan, x, g, gom=None):
     return plan.trajectory_gradient(x, g, gom)
+
+
+def nufft_forward_batch(plan: NufftPlan, x, y=None):
+    return plan.forward_batch(x, y)
+
+
+def nufft_adjoint_batch(plan: NufftPlan, y, x=None):
+    return plan.adjoint_batch(y, x)
+
+
+def nufft_selfadjoint_batch(plan: NufftPlan, x, out=None):
+    return plan.selfadjoint_batch(x, out)

@@ -141,3 +141,37 @@ def test_multicoil_rejects_bad_coil_shape(nf):
         with pytest.raises(ValueError):
             plan.forward_multicoil(dev(coils[:, :16]), dev(cn(Nd, 1)))
         assert nf.lib.nufft_forward_multicoil(plan.handle, None, 4, None, None) == 1     # EINVAL
+
+
+@pytest.mark.parametrize("name,Nd,Kd,Jd,gen", [
+    ("2d", (32, 32), (64, 64), (6, 6), lambda: W.radial2d_golden(30, 64)),
+    ("3d", (16, 16, 16), (32, 32, 32), (6, 6, 6), lambda: W.kooshball3d(80, 32)),
+])
+def test_batched_operators_equal_single_calls(nf, name, Nd, Kd, Jd, gen):
+    om = gen()
+    nb = 5
+    xs = cn((nb,) + Nd, 21)
+    ys = cn((nb, om.shape[0]), 22)
+    ref = oracle.make_plan(om, Nd, Kd, Jd)
+    with nf.NufftPlan(dev(om), Nd, Kd, Jd) as plan:
+        yb = host(plan.forward_batch(dev(xs)))
+        xb = host(plan.adjoint_batch(dev(ys)))
+        sb = host(plan.selfadjoint_batch(dev(xs)))
+        for b in range(nb):
+            assert rel(yb[b], host(plan.forward(dev(xs[b])))) < 1e-6
+            assert rel(xb[b], host(plan.adjoint(dev(ys[b])))) < 1e-6
+            assert rel(sb[b], host(plan.selfadjoint(dev(xs[b])))) < 1e-6
+            assert rel(yb[b], oracle.forward(ref, xs[b])) < TOL_OP
+            assert rel(xb[b], oracle.adjoint(ref, ys[b])) < TOL_OP
+
+
+def test_single_coil_multicoil_equals_plain_operators(nf):
+    Nd, Kd, om, ref, coils = _multicoil_case(nc=1)
+    x = cn(Nd, 8)
+    y = cn(om.shape[0], 9)
+    with nf.NufftPlan(dev(om), Nd, Kd, (6, 6)) as plan:
+        cd = dev(coils)
+        c128 = coils.astype(np.complex128)
+        assert rel(host(plan.forward_multicoil(cd, dev(x))), X.forward_multicoil(ref, c128, x)) < TOL_OP
+        assert rel(host(plan.adjoint_multicoil(cd, dev(y))), X.adjoint_multicoil(ref, c128, y)) < TOL_OP
+        assert rel(host(plan.selfadjoint_multicoil(cd, dev(x))), X.selfadjoint_multicoil(ref, c128, x)) < TOL_OP

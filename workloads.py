@@ -148,6 +148,20 @@ def coil_maps(nc: int, Nd, seed: int = SEED_COILS) -> np.ndarray:
     return maps
 
 
+def dynamic_radial_frames(n_frames: int = 8, n_samples: int = 512, lo: int = 13, hi: int = 89,
+                          seed: int = SEED_TRAJ):
+    """Golden-angle radial frames with uneven spoke counts drawn from U{lo..hi};
+    the golden-angle sequence continues across frames.  Returns a list of
+    float32 (M_f, 2) trajectories."""
+    rng = np.random.default_rng(seed)
+    counts = rng.integers(lo, hi + 1, size=n_frames)
+    frames, first = [], 0
+    for c in counts:
+        frames.append(radial2d_golden(int(c), n_samples, first_spoke=first))
+        first += int(c)
+    return frames
+
+
 # ---- the named workloads -------------------------------------------------------
 
 WORKLOADS = {
