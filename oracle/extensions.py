@@ -133,3 +133,33 @@ def trajectory_gradient(plan: Plan, x: np.ndarray, g: np.ndarray) -> np.ndarray:
     g = dL/dRe(y) + i dL/dIm(y): dL/dw_{m,a} = Re(conj(g_m) dy_m/dw_{m,a})."""
     dy = forward_domega(plan, x)
     return np.real(np.conj(np.asarray(g, dtype=np.complex128))[:, None] * dy)
+
+
+# ---------------------------------------------------------------- Toeplitz-embedded normal operator
+def toeplitz_kernel(plan: Plan) -> np.ndarray:
+    """Spectrum of the Toeplitz embedding of A^H A (the precomputed normal
+    operator of Section 2.1.5, in the Toeplitz form the paper cites).
+
+    (A^H A x)[n] = sum_n' x[n'] t[n - n'],  t[D] = sum_m exp(i w_m . D).
+    t on D in [-N, N)^d is the adjoint NUFFT of all-ones on an image of size
+    2N (oversampled grid 4N, same J): with centred coordinates q - N it gives
+    t[q - N].  Placed circularly on the 2N grid (t_circ[D mod 2N] = t[D]) its
+    unnormalised DFT is the returned kernel."""
+    from .nufft import make_plan as _mk, adjoint as _adj
+    Nd2 = tuple(2 * N for N in plan.Nd)
+    Kd2 = tuple(4 * N for N in plan.Nd)
+    big = _mk(plan.om, Nd2, Kd2, plan.Jd)
+    x2 = _adj(big, np.ones(plan.M, dtype=np.complex128))
+    t_circ = np.fft.ifftshift(x2)               # move D = 0 (q = N) to index 0
+    return np.fft.fftn(t_circ)
+
+
+def selfadjoint_toeplitz(plan: Plan, T: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """A^H A x by the 2N circular embedding: centred zero-pad of x to the 2N
+    grid, DFT, multiply by the kernel spectrum, inverse DFT, crop."""
+    x = np.asarray(x, dtype=np.complex128)
+    idx = [(np.arange(N) - N // 2) % (2 * N) for N in plan.Nd]
+    z = np.zeros(T.shape, dtype=np.complex128)
+    z[np.ix_(*idx)] = x
+    w = np.fft.ifftn(np.fft.fftn(z) * T)
+    return w[np.ix_(*idx)]

@@ -168,3 +168,25 @@ def test_trajectory_gradient_of_a_quadratic_loss():
     omn[m, a] -= h
     L = lambda o: np.sum(np.abs(oracle.forward(oracle.make_plan(o, Nd, Kd, Jd), x) - y0) ** 2)
     assert abs((L(op) - L(omn)) / (2 * h) - g[m, a]) < 1e-6 * abs(g[m, a]) + 1e-8
+
+
+def test_toeplitz_normal_operator_matches_exact_nudft_normal_operator():
+    for Nd in [(16, 16), (8, 8, 8), (24,)]:
+        d = len(Nd)
+        om = W.uniform_random_om(300, d, seed=3)
+        p = oracle.make_plan(om, Nd, tuple(2 * n for n in Nd), (6,) * d)
+        T = X.toeplitz_kernel(p)
+        x = _cn(Nd)
+        exact = oracle.nudft_adjoint(om, oracle.nudft_forward(om, x), Nd)
+        assert _rel(X.selfadjoint_toeplitz(p, T, x), exact) < 1e-4
+        assert _rel(X.selfadjoint_toeplitz(p, T, x), oracle.selfadjoint(p, x)) < 1e-4
+
+
+def test_toeplitz_normal_operator_is_hermitian():
+    om = W.radial2d_uniform(16, 32)
+    p = oracle.make_plan(om, (16, 16), (32, 32), (6, 6))
+    T = X.toeplitz_kernel(p)
+    a, b = _cn((16, 16)), _cn((16, 16))
+    lhs = np.vdot(X.selfadjoint_toeplitz(p, T, a), b)
+    rhs = np.vdot(a, X.selfadjoint_toeplitz(p, T, b))
+    assert abs(lhs - rhs) < 1e-10 * abs(lhs)
