@@ -226,6 +226,21 @@ def run_workload(nf, torch, name: str, steps: int, warmup: int, dev, flush_bytes
         e1.synchronize()
         sa.append(e0.elapsed_time(e1))
     rows = {"a1_plan_ms": round(plan_ms, 3), "a8_selfadjoint_ms": round(statistics.mean(sa), 5)}
+    # the Toeplitz-embedded normal operator (init once, then per call)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan.toeplitz_init()
+    torch.cuda.synchronize()
+    rows["f4_toeplitz_init_ms"] = round((time.perf_counter() - t0) * 1e3, 3)
+    st_ = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0.record(stream)
+        plan.selfadjoint_toeplitz(xd, xo)
+        e1.record(stream)
+        e1.synchronize()
+        st_.append(e0.elapsed_time(e1))
+    rows["f4_selfadjoint_toeplitz_ms"] = round(statistics.mean(st_), 5)
     if solvers:
         # the reconstruction runs of the paper's solvers on this workload's data
         yd = plan.forward(xd)
@@ -246,6 +261,18 @@ def run_workload(nf, torch, name: str, steps: int, warmup: int, dev, flush_bytes
             e1.synchronize()
             rows[key] = round(e0.elapsed_time(e1), 3)
         rows["a9_solver_settings"] = "CG x0=0; L1TV: inner=2, cg_iters=5, mu=1, lambda=0.01"
+        # the same solves with the Toeplitz normal operator
+        plan.set_normal_operator(True)
+        for key, fn in (("f4_cg_100_iterations_toeplitz_ms", lambda: plan.solve_cg(yd, x0.clone(), maxiter=100)),
+                        ("f4_l1tv_ols_50_iterations_toeplitz_ms",
+                         lambda: plan.solve_l1tv_ols(yd, x0.clone(), maxiter=50, inner=2, cg_iters=5, mu=1.0, lam=0.01))):
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            rows[key] = round(e0.elapsed_time(e1), 3)
+        plan.set_normal_operator(False)
 
     # end to end through the host-buffer entry points (pinned host memory)
     x_h = torch.from_numpy(x).pin_memory()

@@ -271,6 +271,28 @@ int solve_cg_multicoil(nufft_plan_t* plan, const float* coils_dev, int nc, const
                        int maxiter);
 
 /*
+ * Toeplitz-embedded normal operator (Section 2.1.5: the paper precomputes
+ * A^H A for its iterative solvers, citing Fessler et al.'s Toeplitz method).
+ * A^H A is a convolution with t[D] = sum_m exp(i om_m . D), D in (-N, N)^d;
+ * embedded circularly in a grid of period P_i (2 N_i rounded up to a power of
+ * two) it becomes FFT, pointwise product, inverse FFT.
+ *   nufft_toeplitz_init         computes the kernel: the adjoint NUFFT of
+ *                               all-ones on a P image (grid 2P, same J), then
+ *                               its DFT.  Needs 2 P_i <= 1024.  Allocates the
+ *                               P^d spectrum; synchronous.  The kernel carries
+ *                               the NUFFT's accuracy (~1e-6 relative).
+ *   nufft_selfadjoint_toeplitz  out = A^H A x through the embedding.
+ *   nufft_set_normal_operator   mode 0: the solvers (solve_cg, solve_l1tv_*,
+ *                               solve_cg_multicoil) apply V^H V through the
+ *                               grid (default); mode 1: the Toeplitz form
+ *                               (after nufft_toeplitz_init).  nufft_selfadjoint
+ *                               always uses V^H V.
+ */
+int nufft_toeplitz_init(nufft_plan_t* plan);
+int nufft_selfadjoint_toeplitz(nufft_plan_t* plan, const float* x_dev, float* out_dev);
+int nufft_set_normal_operator(nufft_plan_t* plan, int mode);
+
+/*
  * nufft_trajectory_gradient - gradient of a real loss L(y), y = A(om) x, with
  * respect to the trajectory (the forward operator of Section 2.1, Eq. 1,
  * differentiated through the min-max coefficients of Section 2.1.3; the paper

@@ -136,29 +136,38 @@ def trajectory_gradient(plan: Plan, x: np.ndarray, g: np.ndarray) -> np.ndarray:
 
 
 # ---------------------------------------------------------------- Toeplitz-embedded normal operator
+def toeplitz_period(N: int) -> int:
+    """Embedding period: 2N rounded up to a power of two (at least 16)."""
+    P = 16
+    while P < 2 * N:
+        P *= 2
+    return P
+
+
 def toeplitz_kernel(plan: Plan) -> np.ndarray:
     """Spectrum of the Toeplitz embedding of A^H A (the precomputed normal
     operator of Section 2.1.5, in the Toeplitz form the paper cites).
 
     (A^H A x)[n] = sum_n' x[n'] t[n - n'],  t[D] = sum_m exp(i w_m . D).
-    t on D in [-N, N)^d is the adjoint NUFFT of all-ones on an image of size
-    2N (oversampled grid 4N, same J): with centred coordinates q - N it gives
-    t[q - N].  Placed circularly on the 2N grid (t_circ[D mod 2N] = t[D]) its
-    unnormalised DFT is the returned kernel."""
+    With P = toeplitz_period(N) >= 2N per dimension, t on D in [-P/2, P/2)^d is
+    the adjoint NUFFT of all-ones on an image of size P (oversampled grid 2P,
+    same J), whose centred coordinates q - P/2 give t[q - P/2].  Placed
+    circularly on the P grid (t_circ[D mod P] = t[D]) its unnormalised DFT is
+    the returned kernel; the circular convolution equals the linear one on the
+    N^d image because P >= 2N."""
     from .nufft import make_plan as _mk, adjoint as _adj
-    Nd2 = tuple(2 * N for N in plan.Nd)
-    Kd2 = tuple(4 * N for N in plan.Nd)
-    big = _mk(plan.om, Nd2, Kd2, plan.Jd)
+    Pd = tuple(toeplitz_period(N) for N in plan.Nd)
+    big = _mk(plan.om, Pd, tuple(2 * P for P in Pd), plan.Jd)
     x2 = _adj(big, np.ones(plan.M, dtype=np.complex128))
-    t_circ = np.fft.ifftshift(x2)               # move D = 0 (q = N) to index 0
+    t_circ = np.fft.ifftshift(x2)               # move D = 0 (q = P/2) to index 0
     return np.fft.fftn(t_circ)
 
 
 def selfadjoint_toeplitz(plan: Plan, T: np.ndarray, x: np.ndarray) -> np.ndarray:
-    """A^H A x by the 2N circular embedding: centred zero-pad of x to the 2N
-    grid, DFT, multiply by the kernel spectrum, inverse DFT, crop."""
+    """A^H A x by the circular embedding: centred zero-pad of x to the P grid,
+    DFT, multiply by the kernel spectrum, inverse DFT, crop."""
     x = np.asarray(x, dtype=np.complex128)
-    idx = [(np.arange(N) - N // 2) % (2 * N) for N in plan.Nd]
+    idx = [(np.arange(N) - N // 2) % P for N, P in zip(plan.Nd, T.shape)]
     z = np.zeros(T.shape, dtype=np.complex128)
     z[np.ix_(*idx)] = x
     w = np.fft.ifftn(np.fft.fftn(z) * T)

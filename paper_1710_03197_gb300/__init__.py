@@ -41,6 +41,9 @@ from .plan import (
     nufft_forward_batch,
     nufft_adjoint_batch,
     nufft_selfadjoint_batch,
+    nufft_toeplitz_init,
+    nufft_selfadjoint_toeplitz,
+    nufft_set_normal_operator,
 )
 from .autograd import NufftFunction, nufft_apply
 
@@ -53,4 +56,5 @@ __all__ = [
     "nufft_adjoint_multicoil", "nufft_selfadjoint_multicoil", "solve_cg_multicoil",
     "nufft_trajectory_gradient", "NufftFunction", "nufft_apply",
     "nufft_forward_batch", "nufft_adjoint_batch", "nufft_selfadjoint_batch",
+    "nufft_toeplitz_init", "nufft_selfadjoint_toeplitz", "nufft_set_normal_operator",
 ]

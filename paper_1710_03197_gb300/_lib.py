@@ -64,6 +64,9 @@ _SIGS = {
     "nufft_forward_batch": (_i, [_PLAN, _i, _vp, _vp]),
     "nufft_adjoint_batch": (_i, [_PLAN, _i, _vp, _vp]),
     "nufft_selfadjoint_batch": (_i, [_PLAN, _i, _vp, _vp]),
+    "nufft_toeplitz_init": (_i, [_PLAN]),
+    "nufft_selfadjoint_toeplitz": (_i, [_PLAN, _vp, _vp]),
+    "nufft_set_normal_operator": (_i, [_PLAN, _i]),
 }
 
 for _name, (_res, _args) in _SIGS.items():

@@ -42,6 +42,7 @@ struct FftArgs {
   int dst_image;              // inverse last pass: write the image, apply S^H
   int64_t src_bstride;        // batch strides (blockIdx.y selects the batch element)
   int64_t dst_bstride;
+  int scale;                  // 0: no S / S^H (plain zero-pad / crop)
 };
 
 template <bool INV>
@@ -177,7 +178,7 @@ k_fft_pass(const FftArgs A, const int W) {
       rem /= A.lead_N[i];
       const int gi = (n - A.lead_N[i] / 2 + A.lead_K[i]) & (A.lead_K[i] - 1);
       goff += (int64_t)gi * A.lead_stride[i];
-      if (A.src_image || A.dst_image) slead *= A.s_lead[i][n];
+      if (A.scale && (A.src_image || A.dst_image)) slead *= A.s_lead[i][n];
     }
   }
   const int half = A.Na >> 1;
@@ -194,7 +195,7 @@ k_fft_pass(const FftArgs A, const int W) {
         if (in_image) {
           if (A.src_image) {
             const int n = p < half ? p + half : p - L + half;
-            v = cscale(__ldg(&src[o * A.Na + n]), A.s_axis[n] * slead);
+            v = cscale(__ldg(&src[o * A.Na + n]), (A.scale ? A.s_axis[n] : 1.0f) * slead);
           } else {
             v = src[goff + (int64_t)p * stride + in];
           }
@@ -229,7 +230,7 @@ k_fft_pass(const FftArgs A, const int W) {
       if (!in_image) continue;
       if (A.dst_image) {
         const int n = p < half ? p + half : p - L + half;
-        dst[o * A.Na + n] = cscale(v, A.s_axis[n] * slead);
+        dst[o * A.Na + n] = cscale(v, (A.scale ? A.s_axis[n] : 1.0f) * slead);
       } else {
         dst[goff + (int64_t)p * stride + in] = v;
       }
@@ -304,10 +305,11 @@ FftArgs make_args(const nufft_plan_t* p, int a) {
 
 }  // namespace
 
-int launch_fft_forward(nufft_plan_t* p, const float2* x, float2* grid, int nb) {
+int launch_fft_forward(nufft_plan_t* p, const float2* x, float2* grid, int nb, bool scale) {
   const int d = p->g.d;
   for (int a = d - 1; a >= 0; --a) {
     FftArgs A = make_args(p, a);
+    A.scale = scale ? 1 : 0;
     A.src_image = (a == d - 1);
     A.src = A.src_image ? x : grid;
     A.dst = grid;
@@ -321,10 +323,11 @@ int launch_fft_forward(nufft_plan_t* p, const float2* x, float2* grid, int nb) {
   return NUFFT_OK;
 }
 
-int launch_fft_inverse(nufft_plan_t* p, float2* grid, float2* x, int nb) {
+int launch_fft_inverse(nufft_plan_t* p, float2* grid, float2* x, int nb, bool scale) {
   const int d = p->g.d;
   for (int a = 0; a < d; ++a) {
     FftArgs A = make_args(p, a);
+    A.scale = scale ? 1 : 0;
     A.dst_image = (a == d - 1);
     A.src = grid;
     A.dst = A.dst_image ? x : grid;

@@ -97,6 +97,13 @@ struct nufft_plan {
   float* om_sorted;         // [d][M] trajectory in tile-sorted order
   float2* dcoef;            // [sum_i J_i][M] d coef / d omega (allocated on first use)
 
+  // Toeplitz-embedded normal operator (nufft_toeplitz_init)
+  nufft_plan* toep_geom;    // FFT geometry N in a 2N grid, no trajectory
+  float2* toep_T;           // kernel spectrum / (2N)^d on the 2N grid
+  float2* toep_grid;        // [batch][ (2N)^d ] work space
+  int toep_cap;             // batch capacity of toep_grid
+  int normal_op;            // 0: V^H V through the grid, 1: Toeplitz (solvers)
+
   // batched work space (grown on demand): grids, partial tiles, k-space, images
   int batch_cap;
   float2* bgrid;            // [batch_cap][Kprod]
@@ -121,8 +128,9 @@ int cuda_check(nufft_plan_t* p, cudaError_t e, const char* what);
 // ------------------------------------------------------------------ launchers
 // FFT passes (fft.cu).  Forward: grid = F pad(S x).  Inverse: x = S crop(F^H grid).
 // nb > 1 runs nb independent transforms: images nb x N^d, grids nb x K^d.
-int launch_fft_forward(nufft_plan_t* p, const float2* x, float2* grid, int nb = 1);
-int launch_fft_inverse(nufft_plan_t* p, float2* grid, float2* x, int nb = 1);
+// scale = false leaves out S (S^H): a plain centred zero-pad (crop).
+int launch_fft_forward(nufft_plan_t* p, const float2* x, float2* grid, int nb = 1, bool scale = true);
+int launch_fft_inverse(nufft_plan_t* p, float2* grid, float2* x, int nb = 1, bool scale = true);
 
 // Interpolation and gridding (interp.cu).
 // nb > 1: grids nb x K^d, k-space data nb x M, partial tiles in `tiles`
@@ -135,6 +143,9 @@ int ensure_batch(nufft_plan_t* p, int nb);
 int forward_batch_impl(nufft_plan_t* p, int nb, const float2* x, float2* y);
 int adjoint_batch_impl(nufft_plan_t* p, int nb, const float2* y, float2* x);
 int selfadjoint_batch_impl(nufft_plan_t* p, int nb, const float2* x, float2* out);
+
+// Normal operator used by the solvers (toeplitz.cu): V^H V or Toeplitz.
+int normal_op(nufft_plan_t* p, const float2* x, float2* out, int nb = 1);
 
 // Plan-time helpers (plan.cu).
 Points points_view(const nufft_plan_t* p);

@@ -669,6 +669,9 @@ extern "C" int nufft_plan(int d, const int* Nd, const int* Kd, const int* Jd, in
 extern "C" int nufft_plan_destroy(nufft_plan_t* p) {
   if (!p) return NUFFT_OK;
   cudaStreamSynchronize(p->stream);
+  if (p->toep_geom) nufft_plan_destroy(p->toep_geom);
+  if (p->toep_T) cudaFree(p->toep_T);
+  if (p->toep_grid) cudaFree(p->toep_grid);
   free_plan_memory(p);
   delete p;
   return NUFFT_OK;

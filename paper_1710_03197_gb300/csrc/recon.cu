@@ -113,7 +113,7 @@ int selfadjoint_multicoil_impl(nufft_plan_t* p, const float2* coils, int nc, con
   }
   k_coil_mul_all<<<blocks_for(n * nc), kThreads, 0, p->stream>>>(coils, x, imgs, n, nc);
   NUFFT_CUDA_TRY(p, cudaGetLastError());
-  TRY(selfadjoint_batch_impl(p, nc, imgs, res));
+  TRY(normal_op(p, imgs, res, nc));
   k_coil_conj_reduce<<<blocks_for(n), kThreads, 0, p->stream>>>(coils, res, out, n, nc);
   NUFFT_CUDA_TRY(p, cudaGetLastError());
   return NUFFT_OK;

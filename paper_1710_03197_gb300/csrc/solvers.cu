@@ -1,5 +1,8 @@
 // solvers.cu - CG, L1TV-OLS and L1TV-LAD on the NUFFT normal operator.
 //
+// The normal operator A^H A is applied through the grid (V^H V) or, after
+// nufft_toeplitz_init and nufft_set_normal_operator(plan, 1), by its Toeplitz
+// embedding.
 // Section 2.1.5 (normal equation A^H A x = A^H y, Eq. 4), Section 2.2.2 (CG,
 // Eqs. 7-9, both the image-domain form and the paper's own k-space form
 // V^H V k = V^H y followed by x = S^{-1} F^{-1} k), Section 2.2.3 (image
@@ -310,8 +313,8 @@ struct Operator {
 };
 
 int apply_op(nufft_plan_t* p, const Operator& op, const float2* in, float2* out, float2* tmp) {
-  if (!op.tv) return selfadjoint_impl(p, in, out);
-  TRY(selfadjoint_impl(p, in, tmp));
+  if (!op.tv) return normal_op(p, in, out);
+  TRY(normal_op(p, in, tmp));
   const ImgGeom G = img_geom(p);
   k_tv_apply<<<ew_blocks(G.n), kEwThreads, 0, p->stream>>>(out, tmp, in, G, op.mu, op.lam);
   LAUNCH_CHECK(p, "tv apply");
@@ -367,13 +370,13 @@ int l1tv(nufft_plan_t* p, const float2* y, float2* x, int maxiter, int inner, in
       k_shrink_tv<<<ew_blocks(n), kEwThreads, 0, st>>>(x, d0, b0, vstride, G, thr_tv);
       LAUNCH_CHECK(p, "shrink");
       if (lad) {
-        TRY(selfadjoint_impl(p, x, tmp));
+        TRY(normal_op(p, x, tmp));
         k_shrink_data<<<ew_blocks(n), kEwThreads, 0, st>>>(tmp, ahy, df, bf, n, thr_f);
         LAUNCH_CHECK(p, "shrink data");
       }
     }
     // A^H A x of the last inner iteration: LAD already holds it in tmp (same x).
-    if (!lad) TRY(selfadjoint_impl(p, x, tmp));
+    if (!lad) TRY(normal_op(p, x, tmp));
     k_outer<<<ew_blocks(n), kEwThreads, 0, st>>>(ahyk, ahy, tmp, n);
     LAUNCH_CHECK(p, "outer");
   }

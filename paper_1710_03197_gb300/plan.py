@@ -260,6 +260,21 @@ class NufftPlan:
                                           _dev_ptr(out, nb * self.Nprod, "out")), self._h)
         return out
 
+    # ---------------------------------------------------------------- Toeplitz normal operator
+    def toeplitz_init(self):
+        self._sync_stream()
+        check(lib.nufft_toeplitz_init(self._h), self._h)
+
+    def selfadjoint_toeplitz(self, x, out=None):
+        out = torch.empty(self.Nd, dtype=torch.complex64, device=self.device) if out is None else out
+        self._sync_stream()
+        check(lib.nufft_selfadjoint_toeplitz(self._h, _dev_ptr(x, self.Nprod, "x"), _dev_ptr(out, self.Nprod, "out")),
+              self._h)
+        return out
+
+    def set_normal_operator(self, toeplitz: bool):
+        check(lib.nufft_set_normal_operator(self._h, 1 if toeplitz else 0), self._h)
+
     # ---------------------------------------------------------------- trajectory gradient
     def trajectory_gradient(self, x, g, gom=None):
         """Re(conj(g) dy/dom) as an (M, d) float32 tensor (C: nufft_trajectory_gradient)."""
@@ -430,3 +445,15 @@ def nufft_adjoint_batch(plan: NufftPlan, y, x=None):
 
 def nufft_selfadjoint_batch(plan: NufftPlan, x, out=None):
     return plan.selfadjoint_batch(x, out)
+
+
+def nufft_toeplitz_init(plan: NufftPlan):
+    return plan.toeplitz_init()
+
+
+def nufft_selfadjoint_toeplitz(plan: NufftPlan, x, out=None):
+    return plan.selfadjoint_toeplitz(x, out)
+
+
+def nufft_set_normal_operator(plan: NufftPlan, mode: int):
+    return plan.set_normal_operator(bool(mode))

@@ -175,3 +175,62 @@ def test_single_coil_multicoil_equals_plain_operators(nf):
         assert rel(host(plan.forward_multicoil(cd, dev(x))), X.forward_multicoil(ref, c128, x)) < TOL_OP
         assert rel(host(plan.adjoint_multicoil(cd, dev(y))), X.adjoint_multicoil(ref, c128, y)) < TOL_OP
         assert rel(host(plan.selfadjoint_multicoil(cd, dev(x))), X.selfadjoint_multicoil(ref, c128, x)) < TOL_OP
+
+
+@pytest.mark.parametrize("Nd,gen", [
+    ((32, 32), lambda: W.radial2d_golden(40, 64)),
+    ((64, 48), lambda: W.uniform_random_om(4000, 2, seed=41)),
+    ((12, 16, 8), lambda: W.kooshball3d(60, 32)),
+    ((40,), lambda: W.uniform_random_om(300, 1, seed=42)),
+])
+def test_toeplitz_selfadjoint_matches_oracle(nf, Nd, gen):
+    om = gen()
+    d = len(Nd)
+    Kd = tuple(2 * n if 2 * n >= 16 else 16 for n in Nd)
+    Kd = tuple(1 << (k - 1).bit_length() for k in Kd)
+    Jd = (6,) * d
+    ref = oracle.make_plan(om, Nd, Kd, Jd)
+    T = X.toeplitz_kernel(ref)
+    x = cn(Nd, 43)
+    with nf.NufftPlan(dev(om), Nd, Kd, Jd) as plan:
+        plan.toeplitz_init()
+        out = host(plan.selfadjoint_toeplitz(dev(x)))
+    assert rel(out, X.selfadjoint_toeplitz(ref, T, x)) < TOL_OP
+    assert rel(out, oracle.selfadjoint(ref, x)) < 1e-4
+
+
+def test_solvers_in_toeplitz_mode_match_oracle(nf):
+    Nd, Kd, Jd = (64, 64), (128, 128), (6, 6)
+    om = W.uniform_random_om(3 * 64 * 64, 2, seed=3)
+    ref = oracle.make_plan(om, Nd, Kd, Jd)
+    T = X.toeplitz_kernel(ref)
+    y = oracle.forward(ref, W.complex_normal_image(Nd)).astype(np.complex64)
+    from oracle.solvers import cg_solve
+    x_ref = cg_solve(lambda v: X.selfadjoint_toeplitz(ref, T, v), oracle.adjoint(ref, y), np.zeros(Nd), 30)
+    coils = W.coil_maps(4, Nd)
+    c128 = coils.astype(np.complex128)
+    ymc = X.forward_multicoil(ref, c128, W.complex_normal_image(Nd)).astype(np.complex64)
+    mc_ref = cg_solve(lambda v: sum(np.conj(c) * X.selfadjoint_toeplitz(ref, T, c * v) for c in c128),
+                      X.adjoint_multicoil(ref, c128, ymc), np.zeros(Nd), 15)
+    with nf.NufftPlan(dev(om), Nd, Kd, Jd) as plan:
+        plan.toeplitz_init()
+        plan.set_normal_operator(True)
+        x = host(plan.solve_cg(dev(y), maxiter=30))
+        xm = host(plan.solve_cg_multicoil(dev(coils), dev(ymc), maxiter=15))
+        plan.set_normal_operator(False)
+        x_grid = host(plan.solve_cg(dev(y), maxiter=30))
+    assert rel(x, x_ref) < TOL_SOLVER
+    assert rel(xm, mc_ref) < TOL_SOLVER
+    assert rel(x_grid, oracle.cg(ref, y, np.zeros(Nd), 30)) < TOL_SOLVER
+
+
+def test_toeplitz_errors(nf):
+    om = W.uniform_random_om(100, 2, seed=44)
+    with nf.NufftPlan(dev(om), (16, 16), (32, 32), (6, 6)) as plan:
+        with pytest.raises(nf.NufftError):
+            plan.selfadjoint_toeplitz(dev(cn((16, 16), 1)))
+        with pytest.raises(nf.NufftError):
+            plan.set_normal_operator(True)
+    with nf.NufftPlan(dev(om), (512, 16), (1024, 32), (6, 6)) as plan:
+        with pytest.raises(nf.NufftError):
+            plan.toeplitz_init()                 # period P = 1024, grid 2P = 2048 exceeds the FFT sizes
