@@ -197,24 +197,27 @@ def run_workload(nf, torch, name: str, steps: int, warmup: int, dev, flush_bytes
         plan.ifft_crop_rescale(grid, xo)
         e[4].record(stream)
     torch.cuda.synchronize()
-    step_ms = [ev[k][0].elapsed_time(ev[k][-1]) for k in range(steps)]
+    staged_ms = [ev[k][0].elapsed_time(ev[k][-1]) for k in range(steps)]
     stage_ms = {s: [ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(steps)] for i, s in enumerate(STAGES)}
 
-    # monolithic entry points, same work (checked to agree with the staged step)
-    for _ in range(2):
+    # The timed step: the operator entry points a user calls (nufft_forward,
+    # nufft_adjoint), which replay their recorded CUDA graphs after the first
+    # two calls.  The staged loop above gives the per-stage breakdown.
+    for _ in range(max(3, warmup)):
         plan.forward(xd, y)
         plan.adjoint(y, xo)
+        flush.fill_(1.0)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    mono = []
+    evm = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for k in range(steps):
         flush.fill_(float(k))
-        e0.record(stream)
+        evm[k][0].record(stream)
         plan.forward(xd, y)
         plan.adjoint(y, xo)
-        e1.record(stream)
-        e1.synchronize()
-        mono.append(e0.elapsed_time(e1))
+        evm[k][1].record(stream)
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in evm]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     # the self-adjoint operator A^H A (one call per step, L2 flushed between)
     sa = []
@@ -288,7 +291,7 @@ def run_workload(nf, torch, name: str, steps: int, warmup: int, dev, flush_bytes
     e2e_s = (time.perf_counter() - t0) / steps
     nprod = int(np.prod(spec["Nd"]))
     plan.close()
-    return dict(spec=spec, info=info, step_ms=step_ms, stage_ms=stage_ms, mono_ms=mono, e2e_s=e2e_s,
+    return dict(spec=spec, info=info, step_ms=step_ms, stage_ms=stage_ms, staged_ms=staged_ms, e2e_s=e2e_s,
                 h2d=8 * (nprod + M), d2h=8 * (M + nprod), rows=rows)
 
 
@@ -372,14 +375,15 @@ def ours(args):
         "warmup": args.warmup, "ms_per_step": round(elapsed * 1e3 / args.steps, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
         "config": {"workload": WORKLOAD_TEXT[names[0]],
-                   "step": "A x then A^H y (forward + adjoint)", "l2": "flushed between timed steps (512 MB write)",
+                   "step": "A x then A^H y (nufft_forward + nufft_adjoint, recorded CUDA graphs replayed)",
+                   "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": round(e2e_units / e2e_el, 1), "unit": UNIT, "h2d_bytes_per_step": res2["h2d"],
                 "d2h_bytes_per_step": res2["d2h"]},
         "gpu_launches": launches_per_step(res2["spec"], res2["info"]["nchunks"]) * args.steps,
         "roofline": roof2,
         "stages": stages2,
-        "monolithic_ms_per_step": round(statistics.mean(res2["mono_ms"]), 5),
+        "staged_ms_per_step": round(statistics.mean(res2["staged_ms"]), 5),
         "rows": res2["rows"],
         "next_rows": next_rows,
         "clocks": clk.summary(),
@@ -394,7 +398,7 @@ def ours(args):
                     "d2h_bytes_per_step": res3["d2h"]},
             "gpu_launches": launches_per_step(res3["spec"], res3["info"]["nchunks"]) * args.steps,
             "roofline": roof3, "stages": stages3, "rows": res3["rows"],
-            "monolithic_ms_per_step": round(statistics.mean(res3["mono_ms"]), 5)}}
+            "staged_ms_per_step": round(statistics.mean(res3["staged_ms"]), 5)}}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

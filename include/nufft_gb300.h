@@ -28,6 +28,14 @@
  * - Every call returns a status; on failure nufft_last_error() describes it.
  * - A plan is not thread-safe: do not call into one plan from two host
  *   threads at once.  Distinct plans are independent.
+ * - CUDA graphs: nufft_forward, nufft_adjoint, nufft_selfadjoint, the batch
+ *   calls and solve_cg record their kernel sequence into a CUDA graph on the
+ *   second call with the same buffers and stream, and replay it afterwards
+ *   (one launch instead of up to a dozen per operator, and hundreds per
+ *   solve).  The first call runs eagerly and does any lazy allocation.  When
+ *   the stream is already being captured by the caller, the calls launch
+ *   normally into the caller's capture.  nufft_set_graphs(plan, 0) turns
+ *   recording off.
  */
 #ifndef NUFFT_GB300_H
 #define NUFFT_GB300_H
@@ -90,6 +98,10 @@ const char* nufft_last_error(const nufft_plan_t* plan);
 
 /* Change the stream the plan's work is ordered on (cudaStream_t as void*). */
 int nufft_set_stream(nufft_plan_t* plan, void* stream);
+
+/* Turn graph recording and replay on (1, the default) or off (0, also drops
+ * the recorded graphs).  See "CUDA graphs" above. */
+int nufft_set_graphs(nufft_plan_t* plan, int enable);
 
 /*
  * Plan description.  info receives 16 int64 values:

@@ -49,6 +49,7 @@ int adjoint_dev(nufft_plan_t* p, const float2* y, float2* x) { return adjoint_im
 // Batched work space for nb transforms at once (grown on demand, kept).
 int ensure_batch(nufft_plan_t* p, int nb) {
   if (nb <= p->batch_cap) return NUFFT_OK;
+  drop_graphs(p);   // graphs may reference the buffers freed below
   for (float2** b : {&p->bgrid, &p->btiles, &p->bytmp, &p->bimg})
     if (*b) { cudaFree(*b); *b = nullptr; }
   p->batch_cap = 0;
@@ -95,14 +96,18 @@ extern "C" int nufft_forward(nufft_plan_t* p, const float* x_dev, float* y_dev) 
   TRY(check_plan(p));
   TRY(check_ptr(p, x_dev, p->Nprod, "x_dev"));
   TRY(check_ptr(p, y_dev, p->M, "y_dev"));
-  return forward_impl(p, reinterpret_cast<const float2*>(x_dev), reinterpret_cast<float2*>(y_dev));
+  const float2* x = reinterpret_cast<const float2*>(x_dev);
+  float2* y = reinterpret_cast<float2*>(y_dev);
+  return run_graphed(p, 1, x, y, 0, [&]() { return forward_impl(p, x, y); });
 }
 
 extern "C" int nufft_adjoint(nufft_plan_t* p, const float* y_dev, float* x_dev) {
   TRY(check_plan(p));
   TRY(check_ptr(p, y_dev, p->M, "y_dev"));
   TRY(check_ptr(p, x_dev, p->Nprod, "x_dev"));
-  return adjoint_impl(p, reinterpret_cast<const float2*>(y_dev), reinterpret_cast<float2*>(x_dev));
+  const float2* y = reinterpret_cast<const float2*>(y_dev);
+  float2* x = reinterpret_cast<float2*>(x_dev);
+  return run_graphed(p, 2, y, x, 0, [&]() { return adjoint_impl(p, y, x); });
 }
 
 extern "C" int nufft_selfadjoint(nufft_plan_t* p, const float* x_dev, float* out_dev) {
@@ -110,7 +115,9 @@ extern "C" int nufft_selfadjoint(nufft_plan_t* p, const float* x_dev, float* out
   TRY(check_ptr(p, x_dev, p->Nprod, "x_dev"));
   TRY(check_ptr(p, out_dev, p->Nprod, "out_dev"));
   if ((const void*)x_dev == (const void*)out_dev) return set_error(p, NUFFT_EINVAL, "x_dev and out_dev alias");
-  return selfadjoint_impl(p, reinterpret_cast<const float2*>(x_dev), reinterpret_cast<float2*>(out_dev));
+  const float2* x = reinterpret_cast<const float2*>(x_dev);
+  float2* out = reinterpret_cast<float2*>(out_dev);
+  return run_graphed(p, 3, x, out, 0, [&]() { return selfadjoint_impl(p, x, out); });
 }
 
 extern "C" int nufft_forward_host(nufft_plan_t* p, const float* x_host, float* y_host) {
@@ -170,7 +177,9 @@ extern "C" int nufft_forward_batch(nufft_plan_t* p, int nb, const float* x_dev, 
   if (nb < 1) return set_error(p, NUFFT_EINVAL, "nb < 1");
   TRY(check_ptr(p, x_dev, p->Nprod, "x_dev"));
   TRY(check_ptr(p, y_dev, p->M, "y_dev"));
-  return forward_batch_impl(p, nb, reinterpret_cast<const float2*>(x_dev), reinterpret_cast<float2*>(y_dev));
+  const float2* x = reinterpret_cast<const float2*>(x_dev);
+  float2* y = reinterpret_cast<float2*>(y_dev);
+  return run_graphed(p, 4, x, y, nb, [&]() { return forward_batch_impl(p, nb, x, y); });
 }
 
 extern "C" int nufft_adjoint_batch(nufft_plan_t* p, int nb, const float* y_dev, float* x_dev) {
@@ -178,7 +187,9 @@ extern "C" int nufft_adjoint_batch(nufft_plan_t* p, int nb, const float* y_dev, 
   if (nb < 1) return set_error(p, NUFFT_EINVAL, "nb < 1");
   TRY(check_ptr(p, y_dev, p->M, "y_dev"));
   TRY(check_ptr(p, x_dev, p->Nprod, "x_dev"));
-  return adjoint_batch_impl(p, nb, reinterpret_cast<const float2*>(y_dev), reinterpret_cast<float2*>(x_dev));
+  const float2* y = reinterpret_cast<const float2*>(y_dev);
+  float2* x = reinterpret_cast<float2*>(x_dev);
+  return run_graphed(p, 5, y, x, nb, [&]() { return adjoint_batch_impl(p, nb, y, x); });
 }
 
 extern "C" int nufft_selfadjoint_batch(nufft_plan_t* p, int nb, const float* x_dev, float* out_dev) {
@@ -187,5 +198,7 @@ extern "C" int nufft_selfadjoint_batch(nufft_plan_t* p, int nb, const float* x_d
   TRY(check_ptr(p, x_dev, p->Nprod, "x_dev"));
   TRY(check_ptr(p, out_dev, p->Nprod, "out_dev"));
   if ((const void*)x_dev == (const void*)out_dev) return set_error(p, NUFFT_EINVAL, "x_dev and out_dev alias");
-  return selfadjoint_batch_impl(p, nb, reinterpret_cast<const float2*>(x_dev), reinterpret_cast<float2*>(out_dev));
+  const float2* x = reinterpret_cast<const float2*>(x_dev);
+  float2* out = reinterpret_cast<float2*>(out_dev);
+  return run_graphed(p, 6, x, out, nb, [&]() { return selfadjoint_batch_impl(p, nb, x, out); });
 }

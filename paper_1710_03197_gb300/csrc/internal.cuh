@@ -55,6 +55,21 @@ struct Chunk {
 
 }  // namespace nufft
 
+namespace nufft {
+// One cached executable graph of an entry point's launch sequence.
+struct GraphEntry {
+  int kind;                 // 0 = free slot
+  const void* a;
+  const void* b;
+  int64_t extra;
+  cudaStream_t stream;
+  int state;                // 1: seen once (ran eagerly), 2: graph ready, 3: never graph
+  cudaGraphExec_t exec;
+  uint64_t last_use;
+};
+constexpr int kGraphSlots = 16;
+}  // namespace nufft
+
 struct nufft_plan {
   nufft::Geom g;
   int64_t M;
@@ -104,6 +119,12 @@ struct nufft_plan {
   int toep_cap;             // batch capacity of toep_grid
   int normal_op;            // 0: V^H V through the grid, 1: Toeplitz (solvers)
 
+  // CUDA graphs of the entry points' launch sequences (see run_graphed)
+  int graphs_enabled;
+  cudaStream_t capture_stream;
+  nufft::GraphEntry graphs[nufft::kGraphSlots];
+  uint64_t graph_clock;
+
   // batched work space (grown on demand): grids, partial tiles, k-space, images
   int batch_cap;
   float2* bgrid;            // [batch_cap][Kprod]
@@ -143,6 +164,20 @@ int ensure_batch(nufft_plan_t* p, int nb);
 int forward_batch_impl(nufft_plan_t* p, int nb, const float2* x, float2* y);
 int adjoint_batch_impl(nufft_plan_t* p, int nb, const float2* y, float2* x);
 int selfadjoint_batch_impl(nufft_plan_t* p, int nb, const float2* x, float2* out);
+
+// CUDA graphs (graphs.cu).  run_graphed runs `body` (which launches work on
+// p->stream) eagerly the first time a (kind, a, b, extra, stream) key is seen,
+// captures it into a graph on a plan-owned stream the second time, and replays
+// the graph into p->stream after that.  Work already being captured by the
+// caller, or a plan with graphs disabled, runs eagerly.  Any change that frees
+// plan-owned buffers must call drop_graphs.
+int run_graphed_impl(nufft_plan_t* p, int kind, const void* a, const void* b, int64_t extra, int (*fn)(void*),
+                     void* ctx);
+template <class F>
+int run_graphed(nufft_plan_t* p, int kind, const void* a, const void* b, int64_t extra, F body) {
+  return run_graphed_impl(p, kind, a, b, extra, [](void* c) -> int { return (*static_cast<F*>(c))(); }, &body);
+}
+void drop_graphs(nufft_plan_t* p);
 
 // Normal operator used by the solvers (toeplitz.cu): V^H V or Toeplitz.
 int normal_op(nufft_plan_t* p, const float2* x, float2* out, int nb = 1);

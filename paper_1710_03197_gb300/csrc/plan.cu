@@ -615,7 +615,7 @@ extern "C" int nufft_plan(int d, const int* Nd, const int* Kd, const int* Jd, in
   Geom g;
   memset(&g, 0, sizeof(g));
   g.d = d;
-  const int base_tile = d == 1 ? 1024 : (d == 2 ? 32 : 16);
+  const int base_tile = d == 1 ? 1024 : 16;
   for (int a = 0; a < d; ++a) {
     const int N = Nd[a], K = Kd[a], J = Jd[a];
     if (!is_pow2(K) || K < kMinK || K > kMaxK)
@@ -654,6 +654,7 @@ extern "C" int nufft_plan(int d, const int* Nd, const int* Kd, const int* Jd, in
   p->Kprod = 1;
   for (int a = 0; a < d; ++a) { p->Nprod *= g.N[a]; p->Kprod *= g.K[a]; }
   p->stream = (cudaStream_t)stream;
+  p->graphs_enabled = 1;
   snprintf(p->err, sizeof(p->err), "no error");
   const int rc = build_plan(p, om_dev);
   if (rc != NUFFT_OK) {
@@ -669,6 +670,8 @@ extern "C" int nufft_plan(int d, const int* Nd, const int* Kd, const int* Jd, in
 extern "C" int nufft_plan_destroy(nufft_plan_t* p) {
   if (!p) return NUFFT_OK;
   cudaStreamSynchronize(p->stream);
+  drop_graphs(p);
+  if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
   if (p->toep_geom) nufft_plan_destroy(p->toep_geom);
   if (p->toep_T) cudaFree(p->toep_T);
   if (p->toep_grid) cudaFree(p->toep_grid);

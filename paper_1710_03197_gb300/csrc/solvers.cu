@@ -390,9 +390,13 @@ extern "C" int solve_cg(nufft_plan_t* p, const float* y_dev, float* x_dev, int m
   if (maxiter < 0) return set_error(p, NUFFT_EINVAL, "maxiter < 0");
   Ws w;
   TRY(get_ws(p, &w));
-  TRY(adjoint_dev(p, reinterpret_cast<const float2*>(y_dev), w.v[V_B]));
-  const Operator op{false, 1.f, 0.f};
-  return cg_run(p, w, op, w.v[V_B], reinterpret_cast<float2*>(x_dev), maxiter);
+  const float2* y = reinterpret_cast<const float2*>(y_dev);
+  float2* x = reinterpret_cast<float2*>(x_dev);
+  return run_graphed(p, 7, y, x, maxiter, [&]() -> int {
+    TRY(adjoint_dev(p, y, w.v[V_B]));
+    const Operator op{false, 1.f, 0.f};
+    return cg_run(p, w, op, w.v[V_B], x, maxiter);
+  });
 }
 
 extern "C" int solve_l1tv_ols(nufft_plan_t* p, const float* y_dev, float* x_dev, int maxiter, int inner,

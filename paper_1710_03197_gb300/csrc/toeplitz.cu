@@ -70,6 +70,7 @@ struct PlanGuard {
 int toeplitz_apply(nufft_plan_t* p, const float2* x, float2* out, int nb) {
   nufft_plan_t* tg = p->toep_geom;
   if (nb > p->toep_cap) {
+    drop_graphs(p);   // graphs may reference the buffer freed below
     if (p->toep_grid) cudaFree(p->toep_grid);
     p->toep_grid = nullptr;
     p->toep_cap = 0;
@@ -183,6 +184,7 @@ extern "C" int nufft_set_normal_operator(nufft_plan_t* p, int mode) {
   if (!p) return set_error(nullptr, NUFFT_EINVAL, "plan is NULL");
   if (mode != 0 && mode != 1) return set_error(p, NUFFT_EINVAL, "mode must be 0 (V^H V) or 1 (Toeplitz)");
   if (mode == 1 && !p->toep_T) return set_error(p, NUFFT_EINVAL, "call nufft_toeplitz_init first");
+  if (mode != p->normal_op) drop_graphs(p);   // recorded solver graphs used the other operator
   p->normal_op = mode;
   return NUFFT_OK;
 }

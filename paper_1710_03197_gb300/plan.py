@@ -90,6 +90,9 @@ class NufftPlan:
     def set_stream(self, stream=None):
         check(lib.nufft_set_stream(self._h, _stream_ptr(stream)), self._h)
 
+    def set_graphs(self, enable: bool):
+        check(lib.nufft_set_graphs(self._h, 1 if enable else 0), self._h)
+
     def _sync_stream(self):
         check(lib.nufft_set_stream(self._h, _stream_ptr()), self._h)
 

@@ -1,0 +1,132 @@
+"""CUDA graph recording and replay inside the library: replayed calls give the
+eager results, a new buffer set records a new graph, growing the batch work
+space drops stale graphs, calls made inside a caller's capture still work, and
+CG replays."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def nf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1710_03197_gb300 as nf
+    return nf
+
+
+def rel(a, b):
+    a, b = np.asarray(a).ravel(), np.asarray(b).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def cn(shape, seed):
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _case():
+    Nd, Kd, Jd = (48, 48), (128, 128), (6, 6)
+    om = W.radial2d_golden(50, 128)
+    return Nd, Kd, Jd, om, oracle.make_plan(om, Nd, Kd, Jd)
+
+
+@pytest.mark.parametrize("side_stream", [False, True])
+def test_replayed_calls_match_eager_and_oracle(nf, side_stream):
+    Nd, Kd, Jd, om, ref = _case()
+    x, yin = cn(Nd, 1), cn(om.shape[0], 2)
+    s = torch.cuda.Stream() if side_stream else torch.cuda.current_stream()
+    with torch.cuda.stream(s):
+        plan = nf.NufftPlan(dev(om), Nd, Kd, Jd)
+        xd, yd = dev(x), dev(yin)
+        y = torch.empty(om.shape[0], dtype=torch.complex64, device=DEV)
+        xo = torch.empty(Nd, dtype=torch.complex64, device=DEV)
+        outs = []
+        for _ in range(4):                       # eager, record, replay, replay
+            y.zero_()
+            xo.zero_()
+            plan.forward(xd, y)
+            plan.adjoint(yd, xo)
+            outs.append((y.clone(), xo.clone()))
+    torch.cuda.synchronize()
+    for yv, xv in outs:
+        assert rel(yv.cpu().numpy(), oracle.forward(ref, x)) < 2e-5
+        assert rel(xv.cpu().numpy(), oracle.adjoint(ref, yin)) < 2e-5
+    plan.close()
+
+
+def test_new_buffers_and_batch_growth(nf):
+    Nd, Kd, Jd, om, ref = _case()
+    plan = nf.NufftPlan(dev(om), Nd, Kd, Jd)
+    x = cn(Nd, 3)
+    xd = dev(x)
+    ys = [torch.empty(om.shape[0], dtype=torch.complex64, device=DEV) for _ in range(3)]
+    for _ in range(3):
+        for y in ys:
+            y.zero_()
+            plan.forward(xd, y)
+    for y in ys:
+        assert rel(y.cpu().numpy(), oracle.forward(ref, x)) < 2e-5
+    # batches of 2, then 4 (work space regrown), then 2 again
+    for nb in (2, 2, 2, 4, 4, 2, 2):
+        xs = cn((nb,) + Nd, 10 + nb)
+        yb = plan.forward_batch(dev(xs))
+        ya = plan.adjoint_batch(yb.contiguous())
+        torch.cuda.synchronize()
+        for b in range(nb):
+            assert rel(yb[b].cpu().numpy(), oracle.forward(ref, xs[b])) < 2e-5
+            assert rel(ya[b].cpu().numpy(), oracle.adjoint(ref, yb[b].cpu().numpy())) < 2e-5
+    plan.close()
+
+
+def test_calls_inside_a_callers_graph_capture(nf):
+    Nd, Kd, Jd, om, ref = _case()
+    plan = nf.NufftPlan(dev(om), Nd, Kd, Jd)
+    x = cn(Nd, 4)
+    xd = dev(x)
+    y = torch.empty(om.shape[0], dtype=torch.complex64, device=DEV)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        plan.forward(xd, y)                      # eager first use on this stream
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            plan.forward(xd, y)
+    y.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert rel(y.cpu().numpy(), oracle.forward(ref, x)) < 2e-5
+    plan.close()
+
+
+def test_cg_replay_matches_first_solve(nf):
+    Nd, Kd, Jd = (64, 64), (128, 128), (6, 6)
+    om = W.uniform_random_om(3 * 64 * 64, 2, seed=3)
+    ref = oracle.make_plan(om, Nd, Kd, Jd)
+    y = oracle.forward(ref, W.complex_normal_image(Nd)).astype(np.complex64)
+    plan = nf.NufftPlan(dev(om), Nd, Kd, Jd)
+    yd = dev(y)
+    x = torch.zeros(Nd, dtype=torch.complex64, device=DEV)
+    res = []
+    for _ in range(3):
+        x.zero_()
+        plan.solve_cg(yd, x, maxiter=15)
+        res.append(x.cpu().numpy().copy())
+    x_ref = oracle.cg(ref, y, np.zeros(Nd), 15)
+    for r in res:
+        assert rel(r, x_ref) < 1e-4
+    plan.set_graphs(False)
+    x.zero_()
+    plan.solve_cg(yd, x, maxiter=15)
+    assert rel(x.cpu().numpy(), x_ref) < 1e-4
+    plan.close()

@@ -97,7 +97,7 @@ def test_tile_sort_and_bank_order(case):
     np.testing.assert_array_equal(np.sort(perm), np.arange(M))
     info = plan.info()
     d = len(case["Nd"])
-    base = {1: 1024, 2: 32, 3: 16}[d]
+    base = {1: 1024, 2: 16, 3: 16}[d]
     T = [min(base, K) for K in case["Kd"]]
     nb = [K // t for K, t in zip(case["Kd"], T)]
     bins = np.zeros(M, dtype=np.int64)
