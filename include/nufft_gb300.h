@@ -28,8 +28,9 @@
  * - Every call returns a status; on failure nufft_last_error() describes it.
  * - A plan is not thread-safe: do not call into one plan from two host
  *   threads at once.  Distinct plans are independent.
- * - CUDA graphs: nufft_forward, nufft_adjoint, nufft_selfadjoint, the batch
- *   calls and solve_cg record their kernel sequence into a CUDA graph on the
+ * - CUDA graphs: nufft_forward, nufft_adjoint, nufft_selfadjoint, their
+ *   host-buffer forms (the kernel part), the stage calls, the batch calls
+ *   and solve_cg record their kernel sequence into a CUDA graph on the
  *   second call with the same buffers and stream, and replay it afterwards
  *   (one launch instead of up to a dozen per operator, and hundreds per
  *   solve).  The first call runs eagerly and does any lazy allocation.  When

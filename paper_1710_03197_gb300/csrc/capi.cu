@@ -125,7 +125,7 @@ extern "C" int nufft_forward_host(nufft_plan_t* p, const float* x_host, float* y
   TRY(check_ptr(p, x_host, p->Nprod, "x_host"));
   TRY(check_ptr(p, y_host, p->M, "y_host"));
   NUFFT_CUDA_TRY(p, cudaMemcpyAsync(p->x_stage, x_host, p->Nprod * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
-  TRY(forward_impl(p, p->x_stage, p->y_stage));
+  TRY(run_graphed(p, 1, p->x_stage, p->y_stage, 0, [&]() { return forward_impl(p, p->x_stage, p->y_stage); }));
   if (p->M > 0)
     NUFFT_CUDA_TRY(p, cudaMemcpyAsync(y_host, p->y_stage, p->M * sizeof(float2), cudaMemcpyDeviceToHost, p->stream));
   NUFFT_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
@@ -138,7 +138,7 @@ extern "C" int nufft_adjoint_host(nufft_plan_t* p, const float* y_host, float* x
   TRY(check_ptr(p, x_host, p->Nprod, "x_host"));
   if (p->M > 0)
     NUFFT_CUDA_TRY(p, cudaMemcpyAsync(p->y_stage, y_host, p->M * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
-  TRY(adjoint_impl(p, p->y_stage, p->x_stage));
+  TRY(run_graphed(p, 2, p->y_stage, p->x_stage, 0, [&]() { return adjoint_impl(p, p->y_stage, p->x_stage); }));
   NUFFT_CUDA_TRY(p, cudaMemcpyAsync(x_host, p->x_stage, p->Nprod * sizeof(float2), cudaMemcpyDeviceToHost, p->stream));
   NUFFT_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
   return NUFFT_OK;
@@ -148,28 +148,36 @@ extern "C" int nufft_scale_pad_fft(nufft_plan_t* p, const float* x_dev, float* g
   TRY(check_plan(p));
   TRY(check_ptr(p, x_dev, p->Nprod, "x_dev"));
   TRY(check_ptr(p, grid_dev, p->Kprod, "grid_dev"));
-  return launch_fft_forward(p, reinterpret_cast<const float2*>(x_dev), reinterpret_cast<float2*>(grid_dev));
+  const float2* x = reinterpret_cast<const float2*>(x_dev);
+  float2* grid = reinterpret_cast<float2*>(grid_dev);
+  return run_graphed(p, 11, x, grid, 0, [&]() { return launch_fft_forward(p, x, grid); });
 }
 
 extern "C" int nufft_interp(nufft_plan_t* p, const float* grid_dev, float* y_dev) {
   TRY(check_plan(p));
   TRY(check_ptr(p, grid_dev, p->Kprod, "grid_dev"));
   TRY(check_ptr(p, y_dev, p->M, "y_dev"));
-  return launch_interp(p, reinterpret_cast<const float2*>(grid_dev), reinterpret_cast<float2*>(y_dev));
+  const float2* grid = reinterpret_cast<const float2*>(grid_dev);
+  float2* y = reinterpret_cast<float2*>(y_dev);
+  return run_graphed(p, 12, grid, y, 0, [&]() { return launch_interp(p, grid, y); });
 }
 
 extern "C" int nufft_gridding(nufft_plan_t* p, const float* y_dev, float* grid_dev) {
   TRY(check_plan(p));
   TRY(check_ptr(p, y_dev, p->M, "y_dev"));
   TRY(check_ptr(p, grid_dev, p->Kprod, "grid_dev"));
-  return launch_gridding(p, reinterpret_cast<const float2*>(y_dev), reinterpret_cast<float2*>(grid_dev));
+  const float2* y = reinterpret_cast<const float2*>(y_dev);
+  float2* grid = reinterpret_cast<float2*>(grid_dev);
+  return run_graphed(p, 13, y, grid, 0, [&]() { return launch_gridding(p, y, grid); });
 }
 
 extern "C" int nufft_ifft_crop_rescale(nufft_plan_t* p, float* grid_dev, float* x_dev) {
   TRY(check_plan(p));
   TRY(check_ptr(p, grid_dev, p->Kprod, "grid_dev"));
   TRY(check_ptr(p, x_dev, p->Nprod, "x_dev"));
-  return launch_fft_inverse(p, reinterpret_cast<float2*>(grid_dev), reinterpret_cast<float2*>(x_dev));
+  float2* grid = reinterpret_cast<float2*>(grid_dev);
+  float2* x = reinterpret_cast<float2*>(x_dev);
+  return run_graphed(p, 14, grid, x, 0, [&]() { return launch_fft_inverse(p, grid, x); });
 }
 
 extern "C" int nufft_forward_batch(nufft_plan_t* p, int nb, const float* x_dev, float* y_dev) {
