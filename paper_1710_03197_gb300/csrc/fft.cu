@@ -16,10 +16,13 @@
 //     the last pass (last axis) applies S^H and writes the image.
 // Padded position of image index n along an axis: g = (n - N/2) mod K.
 //
-// Each line is transformed in shared memory by a Stockham auto-sort FFT
-// (mixed radix: one radix-2 or radix-4 stage, then radix-8 stages), each
-// thread holding 8 values per stage.  Twiddles exp(-2 pi i k / K) come from a
-// table computed in FP64 at plan time.
+// Each line is transformed by a Stockham auto-sort FFT (mixed radix: one
+// radix-2 or radix-4 stage, then radix-8 stages), each thread holding 8 values
+// per stage in registers.  The first stage works on the values as loaded and
+// the last stage's outputs are stored as they are; the hand-offs between
+// stages go through two shared-memory buffers used in turn, one barrier per
+// hand-off.  Twiddles exp(-2 pi i k / K) come from a table computed in FP64 at
+// plan time and are loaded before the barrier of the stage that uses them.
 #include "internal.cuh"
 
 namespace nufft {
@@ -104,42 +107,79 @@ struct SmemMap {
   __device__ __forceinline__ int at(int b, int p) const {
     return STRIDED ? p * (w + 1) + b : b * kLinePitch + p + (p >> 3);
   }
-  static size_t words(int w) { return STRIDED ? (size_t)L * (w + 1) : (size_t)w * kLinePitch; }
+  __host__ __device__ static size_t words(int w) { return STRIDED ? (size_t)L * (w + 1) : (size_t)w * kLinePitch; }
 };
 
-// One Stockham stage of radix R over span Ns, in place in shared memory.
-template <int L, bool STRIDED, bool INV, int R>
-__device__ __forceinline__ void stage(float2* sm, const SmemMap<L, STRIDED> SI, int b, int t, int Ns,
-                                      const float2* __restrict__ tw) {
+// Stockham stage of radix R over span Ns on the values a thread holds.
+//
+// In every stage a thread reads the elements t + k*TPL (k = 0..7) of its line:
+// butterfly q (q < 8/R) takes inputs j + r*L/R with j = t + q*TPL, which is
+// element t + (q + r*Q)*TPL.  So x[k] holds element t + k*TPL on entry, the
+// first stage needs no shared memory, and the outputs of the last stage
+// (Ns = L/R, written to j + r*Ns) are again elements t + k*TPL, stored straight
+// to global memory.  Only the middle hand-offs go through shared memory.
+template <int L, int R>
+struct StageTw {                      // twiddles of one stage, loaded ahead of its barrier
+  float2 w[8 / R][R];
+};
+
+template <int L, bool INV, int R>
+__device__ __forceinline__ void load_twiddles(StageTw<L, R>& T, int t, int Ns, const float2* __restrict__ tw) {
   constexpr int TPL = L / 8;
   constexpr int Q = 8 / R;
-  float2 v[Q][R];
+  const int step = L / (Ns * R);
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
-    const int j = t + q * TPL;
+    const int k = (t + q * TPL) & (Ns - 1);
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[q][r] = sm[SI.at(b, j + r * (L / R))];
+    for (int r = 1; r < R; ++r) {
+      float2 w = __ldg(&tw[r * k * step]);
+      if (INV) w.y = -w.y;
+      T.w[q][r] = w;
+    }
   }
-  __syncthreads();
+}
+
+template <int L, bool INV, int R, bool TW>
+__device__ __forceinline__ void butterflies(float2 (&x)[8], const StageTw<L, R>& T) {
+  constexpr int Q = 8 / R;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = x[q + r * Q];
+    if (TW) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], T.w[q][r]);
+    }
+    dft<R, INV>(v);
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[q + r * Q] = v[r];
+  }
+}
+
+// Write the outputs of a stage (radix R, span Ns) to their Stockham positions.
+template <int L, bool STRIDED, int R>
+__device__ __forceinline__ void write_stage(float2* sm, const SmemMap<L, STRIDED> SI, int b, int t, int Ns,
+                                            const float2 (&x)[8]) {
+  constexpr int TPL = L / 8;
+  constexpr int Q = 8 / R;
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const int j = t + q * TPL;
     const int k = j & (Ns - 1);
-    if (Ns > 1) {
-      const int step = L / (Ns * R);
-#pragma unroll
-      for (int r = 1; r < R; ++r) {
-        float2 w = __ldg(&tw[r * k * step]);
-        if (INV) w.y = -w.y;
-        v[q][r] = cmul(v[q][r], w);
-      }
-    }
-    dft<R, INV>(v[q]);
     const int base = (j - k) * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) sm[SI.at(b, base + r * Ns)] = v[q][r];
+    for (int r = 0; r < R; ++r) sm[SI.at(b, base + r * Ns)] = x[q + r * Q];
   }
-  __syncthreads();
+}
+
+template <int L, bool STRIDED>
+__device__ __forceinline__ void read_own(const float2* sm, const SmemMap<L, STRIDED> SI, int b, int t,
+                                         float2 (&x)[8]) {
+  constexpr int TPL = L / 8;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = sm[SI.at(b, t + k * TPL)];
 }
 
 template <int L, bool STRIDED, bool INV>
@@ -148,6 +188,7 @@ k_fft_pass(const FftArgs A, const int W) {
   constexpr int TPL = L / 8;
   const SmemMap<L, STRIDED> SI{W};
   extern __shared__ float2 sm[];
+  const int bufw = (int)SmemMap<L, STRIDED>::words(W);   // buffer c at sm + c * bufw
 
   const int tid = threadIdx.x;
   int b, t;
@@ -184,7 +225,8 @@ k_fft_pass(const FftArgs A, const int W) {
   const int half = A.Na >> 1;
   const int64_t stride = A.inner;
 
-  // ---- load the line (pruned on the forward side)
+  // ---- load the thread's elements t + k*TPL (pruned on the forward side)
+  float2 x[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const int p = t + k * TPL;
@@ -204,25 +246,47 @@ k_fft_pass(const FftArgs A, const int W) {
         v = src[goff + (int64_t)p * stride + in];
       }
     }
-    sm[SI.at(b, p)] = v;
+    x[k] = v;
   }
-  __syncthreads();
 
-  // ---- transform
+  // ---- transform: an optional radix-2/4 stage, then radix-8 stages
   constexpr int LOG = ilog2(L);
   constexpr int R0 = 1 << (LOG % 3);
+  constexpr int N8 = LOG / 3;
   int Ns = 1;
-  if (R0 == 2) { stage<L, STRIDED, INV, 2>(sm, SI, b, t, Ns, A.tw); Ns *= 2; }
-  if (R0 == 4) { stage<L, STRIDED, INV, 4>(sm, SI, b, t, Ns, A.tw); Ns *= 4; }
+  int cur = 0;
+  if (R0 > 1) {
+    StageTw<L, R0> none;
+    butterflies<L, INV, R0, false>(x, none);
+    write_stage<L, STRIDED, R0>(sm, SI, b, t, 1, x);
+    Ns = R0;
+  }
 #pragma unroll
-  for (int s = 0; s < LOG / 3; ++s) { stage<L, STRIDED, INV, 8>(sm, SI, b, t, Ns, A.tw); Ns *= 8; }
+  for (int s = 0; s < N8; ++s) {
+    StageTw<L, 8> T;
+    const bool first = (R0 == 1 && s == 0);
+    if (!first) {
+      load_twiddles<L, INV, 8>(T, t, Ns, A.tw);
+      __syncthreads();
+      read_own<L, STRIDED>(sm + cur * bufw, SI, b, t, x);
+      butterflies<L, INV, 8, true>(x, T);
+    } else {
+      butterflies<L, INV, 8, false>(x, T);
+    }
+    if (s + 1 < N8) {
+      const int nxt = first ? 0 : cur ^ 1;
+      write_stage<L, STRIDED, 8>(sm + nxt * bufw, SI, b, t, Ns, x);
+      cur = nxt;
+    }
+    Ns *= 8;
+  }
 
-  // ---- store (pruned on the inverse side)
+  // ---- store the thread's elements t + k*TPL (pruned on the inverse side)
   if (!live) return;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const int p = t + k * TPL;
-    const float2 v = sm[SI.at(b, p)];
+    const float2 v = x[k];
     if (!INV) {
       dst[goff + (int64_t)p * stride + in] = v;
     } else {
@@ -250,7 +314,9 @@ cudaError_t launch_L(const FftArgs& A, int nb, cudaStream_t st) {
   int64_t blocks;
   if (STRIDED) {
     W = 8;
-    while (W > 2 && A.nouter * (A.inner / W) < kTargetBlocks) W >>= 1;
+    while (W > 2 && (A.nouter * (A.inner / W) < kTargetBlocks ||
+                     2 * SmemMap<L, STRIDED>::words(W) * sizeof(float2) > 96 * 1024))
+      W >>= 1;
     blocks = A.nouter * (A.inner / W);
   } else {
     W = TPL >= 256 ? 1 : 256 / TPL;
@@ -258,7 +324,7 @@ cudaError_t launch_L(const FftArgs& A, int nb, cudaStream_t st) {
     blocks = (A.nouter + W - 1) / W;
   }
   const int threads = W * TPL;
-  const size_t smem = SmemMap<L, STRIDED>::words(W) * sizeof(float2);
+  const size_t smem = 2 * SmemMap<L, STRIDED>::words(W) * sizeof(float2);   // ping-pong buffers
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_fft_pass<L, STRIDED, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);

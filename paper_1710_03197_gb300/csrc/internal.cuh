@@ -7,6 +7,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <initializer_list>
+
 #include "../../include/nufft_gb300.h"
 
 namespace nufft {
@@ -178,6 +180,23 @@ int run_graphed(nufft_plan_t* p, int kind, const void* a, const void* b, int64_t
   return run_graphed_impl(p, kind, a, b, extra, [](void* c) -> int { return (*static_cast<F*>(c))(); }, &body);
 }
 void drop_graphs(nufft_plan_t* p);
+
+// `extra` of a graph key that carries several parameters: an FNV-1a hash of
+// their bit patterns (pointers and doubles passed through graph_bits).
+inline uint64_t graph_bits(double v) {
+  uint64_t b;
+  memcpy(&b, &v, 8);
+  return b;
+}
+inline uint64_t graph_bits(const void* v) { return (uint64_t)(uintptr_t)v; }
+inline int64_t graph_key(std::initializer_list<uint64_t> vals) {
+  uint64_t h = 1469598103934665603ull;
+  for (uint64_t v : vals) {
+    h ^= v;
+    h *= 1099511628211ull;
+  }
+  return (int64_t)h;
+}
 
 // Normal operator used by the solvers (toeplitz.cu): V^H V or Toeplitz.
 int normal_op(nufft_plan_t* p, const float2* x, float2* out, int nb = 1);

@@ -229,17 +229,16 @@ k_gridding_chunk(const float2* __restrict__ y_b, float2* __restrict__ tiles_b, c
 // neighbours e that reach them are computed once, so every (e, chunk) pair
 // costs one predicated load per cell.  The sum runs over e, then over the
 // source bin's chunks, in a fixed order.
-template <int D, int CPT>
-__global__ void __launch_bounds__(1024)
-k_gridding_reduce(const float2* __restrict__ tiles_b, const int32_t* __restrict__ bin_chunk,
-                  float2* __restrict__ grid_b, const Geom g, const int NG, int64_t tbs, int64_t gbs) {
-  const float2* __restrict__ tiles = tiles_b + (int64_t)blockIdx.y * tbs;
-  float2* __restrict__ grid = grid_b + (int64_t)blockIdx.y * gbs;
+// The whole CTA reduces grid tile `bin`; `part` is shared scratch of
+// blockDim.x * CPT values.  COHERENT reads the partial tiles through L2 only,
+// for tiles written by other CTAs of the same launch.
+template <int D, int CPT, bool COHERENT>
+__device__ __forceinline__ void reduce_tile(const float2* __restrict__ tiles, const int32_t* __restrict__ bin_chunk,
+                                            float2* __restrict__ grid, const Geom& g, const int NG, const int bin,
+                                            float2* part) {
   // NG thread groups of blockDim/NG threads; group h takes every NG-th (e, chunk)
   // pair, and the groups' sums are added in group order at the end.
-  extern __shared__ float2 part[];
   __shared__ int s_q0[1 << kMaxDim], s_q1[1 << kMaxDim], s_delta[1 << kMaxDim];
-  const int bin = blockIdx.x;
   int bc[kMaxDim];
   {
     int rem = bin;
@@ -316,7 +315,7 @@ k_gridding_reduce(const float2* __restrict__ tiles_b, const int32_t* __restrict_
       const float2* src = tiles + (int64_t)q * pc + delta;
 #pragma unroll
       for (int k = 0; k < CPT; ++k)
-        if ((emask[k] >> e) & 1u) acc[k] = cadd(acc[k], __ldg(&src[loc0[k]]));
+        if ((emask[k] >> e) & 1u) acc[k] = cadd(acc[k], COHERENT ? __ldcg(&src[loc0[k]]) : __ldg(&src[loc0[k]]));
     }
     idx += q1 - q0;
   }
@@ -338,6 +337,97 @@ k_gridding_reduce(const float2* __restrict__ tiles_b, const int32_t* __restrict_
     for (int k = 0; k < CPT; ++k)
       if (tg + k * gsize < tile_cells) grid[goff[k]] = acc[k];
   }
+  __syncthreads();   // shared scratch free for the caller
+}
+
+template <int D, int CPT>
+__global__ void __launch_bounds__(1024)
+k_gridding_reduce(const float2* __restrict__ tiles_b, const int32_t* __restrict__ bin_chunk,
+                  float2* __restrict__ grid_b, const Geom g, const int NG, int64_t tbs, int64_t gbs) {
+  extern __shared__ float2 part[];
+  reduce_tile<D, CPT, false>(tiles_b + (int64_t)blockIdx.y * tbs, bin_chunk, grid_b + (int64_t)blockIdx.y * gbs, g,
+                             NG, blockIdx.x, part);
+}
+
+
+// 2D variant: the chunk's point data (first neighbours, coefficients, samples)
+// are first copied into shared memory by all threads at once, so the CTA waits
+// for two dependent global round trips (the permutation, then the samples)
+// instead of one per pass of its warps over the chunk.  The accumulation then
+// follows the same lane layout and bank order as k_gridding_chunk.
+// Shared memory: the split-plane tile, then coef[J0 + J1][cap], y[cap],
+// k[2][cap] (first neighbours relative to the tile origin), cap = chunk size.
+template <int JF>
+__global__ void __launch_bounds__(256, 4)
+k_gridding_chunk_staged(const float2* __restrict__ y_b, float2* __restrict__ tiles_b,
+                        const Chunk* __restrict__ chunks, const Points P, const Geom g, int64_t ybs, int64_t tbs) {
+  constexpr int cap = kChunkPoints[2];
+  extern __shared__ float sm[];
+  const float2* __restrict__ y = y_b + (int64_t)blockIdx.y * ybs;
+  float2* __restrict__ tiles = tiles_b + (int64_t)blockIdx.y * tbs;
+  const int ncell = (int)g.padded_cells;
+  float* sre = sm;
+  float* sim = sm + ncell;
+  const int J0 = JF > 0 ? JF : g.J[0];
+  const int J1 = JF > 0 ? JF : g.J[1];
+  float2* s_c = reinterpret_cast<float2*>(sm + 2 * ncell);   // 8-byte aligned: 2 * ncell floats
+  float2* s_y = s_c + (J0 + J1) * cap;
+  int* s_k = reinterpret_cast<int*>(s_y + cap);
+  const Chunk ch = chunks[blockIdx.x];
+  const int org0 = ((ch.bin >> g.lnb[1]) & (g.nb[0] - 1)) << g.lT[0];
+  const int org1 = (ch.bin & (g.nb[1] - 1)) << g.lT[1];
+
+  for (int c = threadIdx.x; c < 2 * ncell; c += blockDim.x) sm[c] = 0.f;
+  static_assert(cap == 256, "one thread per staged point");
+  const int qs = threadIdx.x;           // the point this thread stages
+  int pm = 0;
+  if (qs < ch.count) {
+    const int q = qs;
+    const int64_t i = (int64_t)ch.start + q;
+    pm = P.perm[i];
+    s_k[q] = P.kf[i] - org0;
+    s_k[cap + q] = P.kf[P.M + i] - org1;
+#pragma unroll
+    for (int r = 0; r < (JF > 0 ? JF : kMaxJ); ++r) {
+      if (JF == 0 && r >= J0) break;
+      s_c[r * cap + q] = P.coef[P.coef_off[0] + (int64_t)r * P.M + i];
+    }
+#pragma unroll
+    for (int r = 0; r < (JF > 0 ? JF : kMaxJ); ++r) {
+      if (JF == 0 && r >= J1) break;
+      s_c[(J0 + r) * cap + q] = P.coef[P.coef_off[1] + (int64_t)r * P.M + i];
+    }
+  }
+  if (qs < ch.count) s_y[qs] = __ldg(&y[pm]);
+  __syncthreads();
+
+  const int G = J1;
+  const int lane = threadIdx.x & 31;
+  const int per_warp = 32 / G;
+  const int sub = lane / G;
+  const int l = lane - sub * G;
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const int P1 = g.P[1];
+  if (sub < per_warp) {
+    for (int q = warp * per_warp + sub; q < ch.count; q += nwarps * per_warp) {
+      const float2 yl = cmulc(s_c[(J0 + l) * cap + q], s_y[q]);   // conj(c_last) * y
+      const int ll = s_k[cap + q] + l;
+      const int l0 = s_k[q];
+#pragma unroll
+      for (int j0 = 0; j0 < (JF > 0 ? JF : kMaxJ); ++j0) {
+        if (JF == 0 && j0 >= J0) break;
+        const float2 w = cmulc(s_c[j0 * cap + q], yl);
+        const int cell = (l0 + j0) * P1 + ll;
+        atomicAdd(&sre[cell], w.x);
+        atomicAdd(&sim[cell], w.y);
+      }
+    }
+  }
+  __syncthreads();
+  float2* out = tiles + (int64_t)blockIdx.x * g.padded_cells;
+  for (int c = threadIdx.x; c < ncell; c += blockDim.x) out[c] = make_float2(sre[c], sim[c]);
+
 }
 
 // The reduction gives every thread 4 cells of the tile; small tiles get up to 4
@@ -370,32 +460,43 @@ cudaError_t interp_d(const nufft_plan_t* p, const float2* grid, float2* y, int n
   const int64_t blocks = (warps * 32 + 255) / 256;
   if (blocks == 0) return cudaSuccess;
   const dim3 gd((unsigned)blocks, (unsigned)nb);
-  if (all_j_equal(p->g, 6)) k_interp<D, 6><<<gd, 256, 0, p->stream>>>(grid, y, P, p->g, p->Kprod, p->M);
-  else k_interp<D, 0><<<gd, 256, 0, p->stream>>>(grid, y, P, p->g, p->Kprod, p->M);
+  auto kern = all_j_equal(p->g, 6) ? k_interp<D, 6> : k_interp<D, 0>;
+  kern<<<gd, 256, 0, p->stream>>>(grid, y, P, p->g, p->Kprod, p->M);
+  return cudaGetLastError();
+}
+
+// Chunk pass of V^H: one CTA per (chunk, batch element), partial tiles out.
+template <int D>
+cudaError_t launch_chunks(const nufft_plan_t* p, const float2* y, float2* tiles, int nb, int64_t ybs, int64_t tbs) {
+  if (p->nchunks == 0) return cudaSuccess;
+  const Points P = points_view(p);
+  const dim3 gd((unsigned)p->nchunks, (unsigned)nb);
+  const bool j6 = all_j_equal(p->g, 6);
+  cudaError_t e;
+  if constexpr (D == 2) {
+    const int sj = p->g.J[0] + p->g.J[1];
+    const size_t smem = (size_t)p->g.padded_cells * sizeof(float2) +
+                        (size_t)kChunkPoints[2] * ((size_t)sj * sizeof(float2) + sizeof(float2) + 2 * sizeof(int));
+    auto kern = j6 ? k_gridding_chunk_staged<6> : k_gridding_chunk_staged<0>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<gd, kChunkPoints[2], smem, p->stream>>>(y, tiles, p->chunks, P, p->g, ybs, tbs);
+  } else {
+    const size_t smem = (size_t)p->g.padded_cells * sizeof(float2);
+    constexpr int NT = GridChunkCfg<D, 6>::kThreads;
+    auto kern = j6 ? k_gridding_chunk<D, 6> : k_gridding_chunk<D, 0>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<gd, NT, smem, p->stream>>>(y, tiles, p->chunks, P, p->g, ybs, tbs);
+  }
   return cudaGetLastError();
 }
 
 template <int D>
 cudaError_t gridding_d(const nufft_plan_t* p, const float2* y, float2* grid, int nb, float2* tiles) {
-  const Points P = points_view(p);
   const int64_t tbs = p->nchunks * p->g.padded_cells;
-  const size_t smem = (size_t)p->g.padded_cells * sizeof(float2);
-  constexpr int NT = GridChunkCfg<D, 6>::kThreads;
-  if (p->nchunks > 0) {
-    if (all_j_equal(p->g, 6)) {
-      cudaError_t e = cudaFuncSetAttribute(k_gridding_chunk<D, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      k_gridding_chunk<D, 6><<<dim3((unsigned)p->nchunks, (unsigned)nb), NT, smem, p->stream>>>(
-          y, tiles, p->chunks, P, p->g, p->M, tbs);
-    } else {
-      cudaError_t e = cudaFuncSetAttribute(k_gridding_chunk<D, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      k_gridding_chunk<D, 0><<<dim3((unsigned)p->nchunks, (unsigned)nb), NT, smem, p->stream>>>(
-          y, tiles, p->chunks, P, p->g, p->M, tbs);
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e = launch_chunks<D>(p, y, tiles, nb, p->M, tbs);
+  if (e != cudaSuccess) return e;
   return launch_reduce<D>(p, tiles, grid, nb);
 }
 
@@ -425,22 +526,8 @@ int static_tiles_address(nufft_plan_t* p, float2** out) {
 
 template <int D>
 cudaError_t gridding_static_d(const nufft_plan_t* p, const float2* y, float2* grid, float2* tiles) {
-  const Points P = points_view(p);
-  const size_t smem = (size_t)p->g.padded_cells * sizeof(float2);
-  constexpr int NT = GridChunkCfg<D, 6>::kThreads;
-  if (p->nchunks > 0) {
-    if (all_j_equal(p->g, 6)) {
-      cudaError_t e = cudaFuncSetAttribute(k_gridding_chunk<D, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      k_gridding_chunk<D, 6><<<(unsigned)p->nchunks, NT, smem, p->stream>>>(y, tiles, p->chunks, P, p->g, 0, 0);
-    } else {
-      cudaError_t e = cudaFuncSetAttribute(k_gridding_chunk<D, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      k_gridding_chunk<D, 0><<<(unsigned)p->nchunks, NT, smem, p->stream>>>(y, tiles, p->chunks, P, p->g, 0, 0);
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e = launch_chunks<D>(p, y, tiles, 1, 0, 0);
+  if (e != cudaSuccess) return e;
   return launch_reduce<D>(p, tiles, grid);
 }
 

@@ -154,26 +154,30 @@ extern "C" int nufft_density_compensation(nufft_plan_t* p, float* w_dev, int ite
   if (p->M == 0) return NUFFT_OK;
   float2 *m0, *m1, *i0, *i1;
   TRY(get_aux(p, &m0, &m1, &i0, &i1));
-  for (int it = 0; it < iters; ++it) {
-    k_real_to_complex<<<blocks_for(p->M), kThreads, 0, p->stream>>>(w_dev, m0, p->M);
-    NUFFT_CUDA_TRY(p, cudaGetLastError());
-    TRY(adjoint_dev(p, m0, i0));
-    TRY(forward_dev(p, i0, m1));
-    k_dcf_update<<<blocks_for(p->M), kThreads, 0, p->stream>>>(w_dev, m1, p->M);
-    NUFFT_CUDA_TRY(p, cudaGetLastError());
-  }
-  return NUFFT_OK;
+  return run_graphed(p, 19, w_dev, nullptr, iters, [&]() -> int {
+    for (int it = 0; it < iters; ++it) {
+      k_real_to_complex<<<blocks_for(p->M), kThreads, 0, p->stream>>>(w_dev, m0, p->M);
+      NUFFT_CUDA_TRY(p, cudaGetLastError());
+      TRY(adjoint_dev(p, m0, i0));
+      TRY(forward_dev(p, i0, m1));
+      k_dcf_update<<<blocks_for(p->M), kThreads, 0, p->stream>>>(w_dev, m1, p->M);
+      NUFFT_CUDA_TRY(p, cudaGetLastError());
+    }
+    return NUFFT_OK;
+  });
 }
 
 extern "C" int nufft_gridding_recon(nufft_plan_t* p, const float* y_dev, const float* w_dev, float* x_dev) {
   TRY(check_plan_ptrs(p, {{y_dev, p ? p->M : 0}, {w_dev, p ? p->M : 0}, {x_dev, p ? p->Nprod : 0}}));
   float2 *m0, *m1, *i0, *i1;
   TRY(get_aux(p, &m0, &m1, &i0, &i1));
-  if (p->M > 0) {
-    k_weight<<<blocks_for(p->M), kThreads, 0, p->stream>>>(reinterpret_cast<const float2*>(y_dev), w_dev, m0, p->M);
-    NUFFT_CUDA_TRY(p, cudaGetLastError());
-  }
-  return adjoint_dev(p, m0, reinterpret_cast<float2*>(x_dev));
+  return run_graphed(p, 20, y_dev, x_dev, graph_key({graph_bits(w_dev)}), [&]() -> int {
+    if (p->M > 0) {
+      k_weight<<<blocks_for(p->M), kThreads, 0, p->stream>>>(reinterpret_cast<const float2*>(y_dev), w_dev, m0, p->M);
+      NUFFT_CUDA_TRY(p, cudaGetLastError());
+    }
+    return adjoint_dev(p, m0, reinterpret_cast<float2*>(x_dev));
+  });
 }
 
 extern "C" int nufft_forward_multicoil(nufft_plan_t* p, const float* coils_dev, int nc, const float* x_dev,
@@ -190,18 +194,22 @@ extern "C" int nufft_forward_multicoil(nufft_plan_t* p, const float* coils_dev, 
     imgs = p->bimg;
   }
   const int64_t n = p->Nprod;
-  k_coil_mul_all<<<blocks_for(n * nc), kThreads, 0, p->stream>>>(reinterpret_cast<const float2*>(coils_dev),
-                                                                 reinterpret_cast<const float2*>(x_dev), imgs, n, nc);
-  NUFFT_CUDA_TRY(p, cudaGetLastError());
-  return forward_batch_impl(p, nc, imgs, reinterpret_cast<float2*>(y_dev));
+  return run_graphed(p, 16, x_dev, y_dev, graph_key({graph_bits(coils_dev), (uint64_t)nc}), [&]() -> int {
+    k_coil_mul_all<<<blocks_for(n * nc), kThreads, 0, p->stream>>>(reinterpret_cast<const float2*>(coils_dev),
+                                                                   reinterpret_cast<const float2*>(x_dev), imgs, n, nc);
+    NUFFT_CUDA_TRY(p, cudaGetLastError());
+    return forward_batch_impl(p, nc, imgs, reinterpret_cast<float2*>(y_dev));
+  });
 }
 
 extern "C" int nufft_adjoint_multicoil(nufft_plan_t* p, const float* coils_dev, int nc, const float* y_dev,
                                        float* x_dev) {
   TRY(check_plan_ptrs(p, {{coils_dev, p ? p->Nprod : 0}, {y_dev, p ? p->M : 0}, {x_dev, p ? p->Nprod : 0}}));
   if (nc < 1) return set_error(p, NUFFT_EINVAL, "nc < 1");
-  return adjoint_multicoil_impl(p, reinterpret_cast<const float2*>(coils_dev), nc,
-                                reinterpret_cast<const float2*>(y_dev), reinterpret_cast<float2*>(x_dev));
+  return run_graphed(p, 17, y_dev, x_dev, graph_key({graph_bits(coils_dev), (uint64_t)nc}), [&]() {
+    return adjoint_multicoil_impl(p, reinterpret_cast<const float2*>(coils_dev), nc,
+                                  reinterpret_cast<const float2*>(y_dev), reinterpret_cast<float2*>(x_dev));
+  });
 }
 
 extern "C" int nufft_selfadjoint_multicoil(nufft_plan_t* p, const float* coils_dev, int nc, const float* x_dev,
@@ -209,6 +217,8 @@ extern "C" int nufft_selfadjoint_multicoil(nufft_plan_t* p, const float* coils_d
   TRY(check_plan_ptrs(p, {{coils_dev, p ? p->Nprod : 0}, {x_dev, p ? p->Nprod : 0}, {out_dev, p ? p->Nprod : 0}}));
   if (nc < 1) return set_error(p, NUFFT_EINVAL, "nc < 1");
   if ((const void*)x_dev == (const void*)out_dev) return set_error(p, NUFFT_EINVAL, "x_dev and out_dev alias");
-  return selfadjoint_multicoil_impl(p, reinterpret_cast<const float2*>(coils_dev), nc,
-                                    reinterpret_cast<const float2*>(x_dev), reinterpret_cast<float2*>(out_dev));
+  return run_graphed(p, 18, x_dev, out_dev, graph_key({graph_bits(coils_dev), (uint64_t)nc}), [&]() {
+    return selfadjoint_multicoil_impl(p, reinterpret_cast<const float2*>(coils_dev), nc,
+                                      reinterpret_cast<const float2*>(x_dev), reinterpret_cast<float2*>(out_dev));
+  });
 }

@@ -337,9 +337,6 @@ int check_common(nufft_plan_t* p, const float* y, const float* x) {
 
 int l1tv(nufft_plan_t* p, const float2* y, float2* x, int maxiter, int inner, int cg_iters, double mu, double lambda,
          bool lad) {
-  if (maxiter < 0 || inner < 1 || cg_iters < 1)
-    return set_error(p, NUFFT_EINVAL, "need maxiter >= 0, inner >= 1, cg_iters >= 1");
-  if (!(mu > 0.0) || !(lambda > 0.0)) return set_error(p, NUFFT_EINVAL, "need mu > 0 and lambda > 0");
   Ws w;
   TRY(get_ws(p, &w));
   const int64_t n = p->Nprod;
@@ -399,18 +396,32 @@ extern "C" int solve_cg(nufft_plan_t* p, const float* y_dev, float* x_dev, int m
   });
 }
 
+namespace {
+
+int l1tv_entry(nufft_plan_t* p, const float* y_dev, float* x_dev, int maxiter, int inner, int cg_iters, double mu,
+               double lambda, bool lad) {
+  TRY(check_common(p, y_dev, x_dev));
+  if (maxiter < 0 || inner < 1 || cg_iters < 1)
+    return set_error(p, NUFFT_EINVAL, "need maxiter >= 0, inner >= 1, cg_iters >= 1");
+  if (!(mu > 0.0) || !(lambda > 0.0)) return set_error(p, NUFFT_EINVAL, "need mu > 0 and lambda > 0");
+  Ws w;
+  TRY(get_ws(p, &w));
+  const float2* y = reinterpret_cast<const float2*>(y_dev);
+  float2* x = reinterpret_cast<float2*>(x_dev);
+  return run_graphed(p, lad ? 9 : 8, y, x, graph_key({(uint64_t)maxiter, (uint64_t)inner, (uint64_t)cg_iters, graph_bits(mu), graph_bits(lambda)}),
+                     [&]() { return l1tv(p, y, x, maxiter, inner, cg_iters, mu, lambda, lad); });
+}
+
+}  // namespace
+
 extern "C" int solve_l1tv_ols(nufft_plan_t* p, const float* y_dev, float* x_dev, int maxiter, int inner,
                               int cg_iters, double mu, double lambda) {
-  TRY(check_common(p, y_dev, x_dev));
-  return l1tv(p, reinterpret_cast<const float2*>(y_dev), reinterpret_cast<float2*>(x_dev), maxiter, inner, cg_iters,
-              mu, lambda, false);
+  return l1tv_entry(p, y_dev, x_dev, maxiter, inner, cg_iters, mu, lambda, false);
 }
 
 extern "C" int solve_l1tv_lad(nufft_plan_t* p, const float* y_dev, float* x_dev, int maxiter, int inner,
                               int cg_iters, double mu, double lambda) {
-  TRY(check_common(p, y_dev, x_dev));
-  return l1tv(p, reinterpret_cast<const float2*>(y_dev), reinterpret_cast<float2*>(x_dev), maxiter, inner, cg_iters,
-              mu, lambda, true);
+  return l1tv_entry(p, y_dev, x_dev, maxiter, inner, cg_iters, mu, lambda, true);
 }
 
 // ------------------------------------------------------------------ k-space CG (Eqs. 7-9)
@@ -429,22 +440,24 @@ extern "C" int solve_cg_kspace(nufft_plan_t* p, const float* y_dev, float* x_dev
   char* base = (char*)p->kspace_ws;
   float2 *b = (float2*)base, *r = (float2*)(base + vb), *pv = (float2*)(base + 2 * vb),
          *q = (float2*)(base + 3 * vb), *k = (float2*)(base + 4 * vb);
-  cudaStream_t st = p->stream;
-  TRY(launch_gridding(p, reinterpret_cast<const float2*>(y_dev), b));          // V^H y
-  NUFFT_CUDA_TRY(p, cudaMemsetAsync(k, 0, n * sizeof(float2), st));
-  auto vhv = [&](const float2* in, float2* out) -> int {                       // V^H V
-    TRY(launch_interp(p, in, p->ytmp));
-    return launch_gridding(p, p->ytmp, out);
-  };
-  TRY(cg_core(p, n, r, pv, q, w.part, w.sc, vhv, b, k, maxiter));
-  TRY(launch_fft_inverse(p, k, reinterpret_cast<float2*>(x_dev)));          // S crop(F^H k)
-  const ImgGeom G = img_geom(p);
-  const float* s1 = p->g.d > 1 ? p->s + p->s_off[1] : p->s;
-  const float* s2 = p->g.d > 2 ? p->s + p->s_off[2] : p->s;
-  k_kspace_finish<<<ew_blocks(G.n), kEwThreads, 0, st>>>(reinterpret_cast<float2*>(x_dev), G, p->s + p->s_off[0], s1,
-                                                        s2, (float)(1.0 / (double)p->Kprod));
-  LAUNCH_CHECK(p, "k-space finish");
-  return NUFFT_OK;
+  return run_graphed(p, 10, y_dev, x_dev, maxiter, [&]() -> int {
+    cudaStream_t st = p->stream;
+    TRY(launch_gridding(p, reinterpret_cast<const float2*>(y_dev), b));          // V^H y
+    NUFFT_CUDA_TRY(p, cudaMemsetAsync(k, 0, n * sizeof(float2), st));
+    auto vhv = [&](const float2* in, float2* out) -> int {                       // V^H V
+      TRY(launch_interp(p, in, p->ytmp));
+      return launch_gridding(p, p->ytmp, out);
+    };
+    TRY(cg_core(p, n, r, pv, q, w.part, w.sc, vhv, b, k, maxiter));
+    TRY(launch_fft_inverse(p, k, reinterpret_cast<float2*>(x_dev)));          // S crop(F^H k)
+    const ImgGeom G = img_geom(p);
+    const float* s1 = p->g.d > 1 ? p->s + p->s_off[1] : p->s;
+    const float* s2 = p->g.d > 2 ? p->s + p->s_off[2] : p->s;
+    k_kspace_finish<<<ew_blocks(G.n), kEwThreads, 0, st>>>(reinterpret_cast<float2*>(x_dev), G, p->s + p->s_off[0],
+                                                          s1, s2, (float)(1.0 / (double)p->Kprod));
+    LAUNCH_CHECK(p, "k-space finish");
+    return NUFFT_OK;
+  });
 }
 
 // ------------------------------------------------------------------ multi-coil CG (Eqs. 32-33)
@@ -456,8 +469,12 @@ extern "C" int solve_cg_multicoil(nufft_plan_t* p, const float* coils_dev, int n
   Ws w;
   TRY(get_ws(p, &w));
   const float2* coils = reinterpret_cast<const float2*>(coils_dev);
-  TRY(adjoint_multicoil_impl(p, coils, nc, reinterpret_cast<const float2*>(y_dev), w.v[V_B]));
-  auto op = [&](const float2* in, float2* out) -> int { return selfadjoint_multicoil_impl(p, coils, nc, in, out); };
-  return cg_core(p, p->Nprod, w.v[V_R], w.v[V_P], w.v[V_Q], w.part, w.sc, op, w.v[V_B],
-                 reinterpret_cast<float2*>(x_dev), maxiter);
+  const float2* y = reinterpret_cast<const float2*>(y_dev);
+  float2* x = reinterpret_cast<float2*>(x_dev);
+  const int64_t key = graph_key({(uint64_t)maxiter, (uint64_t)nc, graph_bits(coils_dev)});
+  return run_graphed(p, 15, y, x, key, [&]() -> int {
+    TRY(adjoint_multicoil_impl(p, coils, nc, y, w.v[V_B]));
+    auto op = [&](const float2* in, float2* out) -> int { return selfadjoint_multicoil_impl(p, coils, nc, in, out); };
+    return cg_core(p, p->Nprod, w.v[V_R], w.v[V_P], w.v[V_Q], w.part, w.sc, op, w.v[V_B], x, maxiter);
+  });
 }

@@ -130,3 +130,53 @@ def test_cg_replay_matches_first_solve(nf):
     plan.solve_cg(yd, x, maxiter=15)
     assert rel(x.cpu().numpy(), x_ref) < 1e-4
     plan.close()
+
+
+def test_solver_and_recon_replays_match_eager(nf):
+    """Every graphed solver and reconstruction entry point: the eager first
+    call, the recording second call and the replays agree, and a change of a
+    scalar parameter (lambda, iterations, coil set) selects its own graph."""
+    Nd, Kd, Jd = (32, 32), (64, 64), (6, 6)
+    om = W.uniform_random_om(3 * 32 * 32, 2, seed=5)
+    ref = oracle.make_plan(om, Nd, Kd, Jd)
+    y = dev(oracle.forward(ref, W.complex_normal_image(Nd)).astype(np.complex64))
+    coils = dev(W.coil_maps(3, Nd))
+    coils2 = dev(W.coil_maps(2, Nd))
+    ymc = dev(cn(3 * om.shape[0], 7))
+    wts = dev(np.abs(cn(om.shape[0], 8)).astype(np.float32))
+    calls = {
+        "ols_a": lambda p, x: p.solve_l1tv_ols(y, x, maxiter=4, inner=2, cg_iters=3, mu=1.0, lam=0.05),
+        "ols_b": lambda p, x: p.solve_l1tv_ols(y, x, maxiter=4, inner=2, cg_iters=3, mu=1.0, lam=50.0),
+        "lad": lambda p, x: p.solve_l1tv_lad(y, x, maxiter=4, inner=2, cg_iters=3, mu=1.0, lam=0.05),
+        "kspace": lambda p, x: p.solve_cg_kspace(y, x, maxiter=8),
+        "mc_cg": lambda p, x: p.solve_cg_multicoil(coils, ymc, x, maxiter=8),
+        "mc_adj": lambda p, x: p.adjoint_multicoil(coils, ymc, x),
+        "mc_self": lambda p, x: p.selfadjoint_multicoil(coils2, y[:Nd[0] * Nd[1]].view(Nd), x),
+        "recon": lambda p, x: p.gridding_recon(y, wts, x),
+    }
+    eager = {}
+    with nf.NufftPlan(dev(om), Nd, Kd, Jd) as plan:
+        plan.set_graphs(False)
+        for name, fn in calls.items():
+            x = torch.zeros(Nd, dtype=torch.complex64, device=DEV)
+            fn(plan, x)
+            eager[name] = x.cpu().numpy()
+        w_eager = plan.density_compensation(1).cpu().numpy()
+    with nf.NufftPlan(dev(om), Nd, Kd, Jd) as plan:
+        xs = {name: torch.zeros(Nd, dtype=torch.complex64, device=DEV) for name in calls}
+        for _ in range(3):                       # eager, record, replay; the calls interleave
+            for name, fn in calls.items():
+                xs[name].zero_()
+                fn(plan, xs[name])
+            torch.cuda.synchronize()
+            for name in calls:
+                assert rel(xs[name].cpu().numpy(), eager[name]) < 1e-5, name
+        w = torch.ones(om.shape[0], dtype=torch.float32, device=DEV)
+        for _ in range(3):
+            w.fill_(1.0)
+            # one Pipe-Menon step: later steps divide by |A A^H w| where it
+            # cancels and amplify the run-to-run order of shared-memory atomics
+            plan.density_compensation(1, w)
+            torch.cuda.synchronize()
+            assert rel(w.cpu().numpy(), w_eager) < 1e-5
+    assert rel(eager["ols_a"], eager["ols_b"]) > 1e-3     # lambda matters, so the key must carry it
