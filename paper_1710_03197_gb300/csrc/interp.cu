@@ -117,14 +117,19 @@ struct GridChunkCfg {
   static constexpr int kMinBlocks = D == 3 ? (JF == 6 ? 3 : 2) : 4;
 };
 
-template <int D, int JF>
+// TF > 0: every tile edge is TF and every J is JF, so the padded-tile pitches
+// are compile-time constants and the neighbour loops unroll into fixed
+// shared-memory offsets.
+template <int D, int JF, int TF>
 __global__ void __launch_bounds__(GridChunkCfg<D, JF>::kThreads, GridChunkCfg<D, JF>::kMinBlocks)
 k_gridding_chunk(const float2* __restrict__ y_b, float2* __restrict__ tiles_b, const Chunk* __restrict__ chunks,
                  const Points P, const Geom g, int64_t ybs, int64_t tbs) {
+  static_assert(TF == 0 || JF > 0, "a fixed tile needs a fixed J");
+  constexpr int PF = TF > 0 ? TF + JF - 1 : 0;   // padded edge when fixed
   extern __shared__ float sm[];
   const float2* __restrict__ y = y_b + (int64_t)blockIdx.y * ybs;
   float2* __restrict__ tiles = tiles_b + (int64_t)blockIdx.y * tbs;
-  const int ncell = (int)g.padded_cells;
+  const int ncell = TF > 0 ? (D == 1 ? PF : (D == 2 ? PF * PF : PF * PF * PF)) : (int)g.padded_cells;
   float* sre = sm;
   float* sim = sm + ncell;
   const Chunk ch = chunks[blockIdx.x];
@@ -147,8 +152,8 @@ k_gridding_chunk(const float2* __restrict__ y_b, float2* __restrict__ tiles_b, c
   const int l = lane - sub * G;
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
-  const int P1 = D > 1 ? g.P[1] : 1;
-  const int P2 = D > 2 ? g.P[2] : 1;
+  const int P1 = D > 1 ? (TF > 0 ? PF : g.P[1]) : 1;
+  const int P2 = D > 2 ? (TF > 0 ? PF : g.P[2]) : 1;
 
   // Consecutive points of the chunk share a warp instruction: the plan orders
   // each chunk so that every aligned group of per_warp points covers disjoint
@@ -199,7 +204,8 @@ k_gridding_chunk(const float2* __restrict__ y_b, float2* __restrict__ tiles_b, c
           if (JF == 0 && j1 >= J1) break;
           c1v[j1] = P.coef[P.coef_off[1] + (int64_t)j1 * P.M + i];
         }
-#pragma unroll 1
+        constexpr int kU0 = TF > 0 ? JF : 1;
+#pragma unroll kU0
         for (int j0 = 0; j0 < J0; ++j0) {
           const float2 c0 = P.coef[P.coef_off[0] + (int64_t)j0 * P.M + i];
           const float2 w0 = cmulc(c0, yl);
@@ -484,7 +490,10 @@ cudaError_t launch_chunks(const nufft_plan_t* p, const float2* y, float2* tiles,
   } else {
     const size_t smem = (size_t)p->g.padded_cells * sizeof(float2);
     constexpr int NT = GridChunkCfg<D, 6>::kThreads;
-    auto kern = j6 ? k_gridding_chunk<D, 6> : k_gridding_chunk<D, 0>;
+    bool t16 = D == 3;
+    for (int a = 0; a < D; ++a) t16 = t16 && p->g.T[a] == 16;
+    auto kern = j6 ? (t16 ? k_gridding_chunk<D, 6, (D == 3 ? 16 : 0)> : k_gridding_chunk<D, 6, 0>)
+                   : k_gridding_chunk<D, 0, 0>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<gd, NT, smem, p->stream>>>(y, tiles, p->chunks, P, p->g, ybs, tbs);
