@@ -155,7 +155,8 @@ WORKLOAD_TEXT = {
 }
 
 
-def run_workload(nf, torch, name: str, steps: int, warmup: int, dev, flush_bytes: int, solvers: bool = False):
+def run_workload(nf, torch, name: str, steps: int, warmup: int, dev, flush_bytes: int, solvers: bool = False,
+                 extra_rows: bool = True):
     spec, om, x, noise = W.make_workload(name)
     M = spec["M"]
     om_d = torch.from_numpy(om).to(dev)
@@ -251,8 +252,33 @@ def run_workload(nf, torch, name: str, steps: int, warmup: int, dev, flush_bytes
         evm[k][1].record(stream)
     torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in evm]
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
+    rows = {"a1_plan_ms": round(plan_ms, 3)}
+    if extra_rows:
+        rows.update(_extra_rows(plan, torch, spec, x, xd, xo, noise, steps, flush, stream, dev, solvers))
+
+    # end to end through the host-buffer entry points (pinned host memory)
+    x_h = torch.from_numpy(x).pin_memory()
+    y_h = torch.empty(M, dtype=torch.complex64).pin_memory()
+    xo_h = torch.empty(spec["Nd"], dtype=torch.complex64).pin_memory()
+    for _ in range(2):
+        plan.forward_host(x_h, y_h)
+        plan.adjoint_host(y_h, xo_h)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        plan.forward_host(x_h, y_h)
+        plan.adjoint_host(y_h, xo_h)
+    e2e_s = (time.perf_counter() - t0) / steps
+    nprod = int(np.prod(spec["Nd"]))
+    plan.close()
+    return dict(spec=spec, info=info, step_ms=step_ms, stage_ms=stage_ms, staged_ms=staged_ms, e2e_s=e2e_s,
+                stage_timing=stage_timing,
+                h2d=8 * (nprod + M), d2h=8 * (M + nprod), rows=rows)
+
+
+def _extra_rows(plan, torch, spec, x, xd, xo, noise, steps, flush, stream, dev, solvers):
+    """Rows beyond the timed step: A^H A, the Toeplitz operator, the solvers."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     # the self-adjoint operator A^H A (one call per step, L2 flushed between)
     sa = []
     for k in range(steps):
@@ -262,7 +288,7 @@ def run_workload(nf, torch, name: str, steps: int, warmup: int, dev, flush_bytes
         e1.record(stream)
         e1.synchronize()
         sa.append(e0.elapsed_time(e1))
-    rows = {"a1_plan_ms": round(plan_ms, 3), "a8_selfadjoint_ms": round(statistics.mean(sa), 5)}
+    rows = {"a8_selfadjoint_ms": round(statistics.mean(sa), 5)}
     # the Toeplitz-embedded normal operator (init once, then per call)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -310,24 +336,7 @@ def run_workload(nf, torch, name: str, steps: int, warmup: int, dev, flush_bytes
             e1.synchronize()
             rows[key] = round(e0.elapsed_time(e1), 3)
         plan.set_normal_operator(False)
-
-    # end to end through the host-buffer entry points (pinned host memory)
-    x_h = torch.from_numpy(x).pin_memory()
-    y_h = torch.empty(M, dtype=torch.complex64).pin_memory()
-    xo_h = torch.empty(spec["Nd"], dtype=torch.complex64).pin_memory()
-    for _ in range(2):
-        plan.forward_host(x_h, y_h)
-        plan.adjoint_host(y_h, xo_h)
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        plan.forward_host(x_h, y_h)
-        plan.adjoint_host(y_h, xo_h)
-    e2e_s = (time.perf_counter() - t0) / steps
-    nprod = int(np.prod(spec["Nd"]))
-    plan.close()
-    return dict(spec=spec, info=info, step_ms=step_ms, stage_ms=stage_ms, staged_ms=staged_ms, e2e_s=e2e_s,
-                stage_timing=stage_timing,
-                h2d=8 * (nprod + M), d2h=8 * (M + nprod), rows=rows)
+    return rows
 
 
 def roofline_for(res, peak_gbs: float, peak_kind: str, traffic: dict):
@@ -367,9 +376,10 @@ def ours(args):
     names = [w.strip() for w in args.workloads.split(",") if w.strip()]
     with ClockSampler(torch.cuda.current_device() if world == 1 else local, clocks_path) as clk:
         results = {n: run_workload(nf, torch, n, args.steps, args.warmup, dev, flush_bytes,
-                                   solvers=(i == 0 and not args.no_solvers)) for i, n in enumerate(names)}
+                                   solvers=(i == 0 and not args.no_solvers), extra_rows=not args.no_rows)
+                   for i, n in enumerate(names)}
         next_rows = None
-        if not args.no_solvers:
+        if not args.no_solvers and not args.no_rows:
             next_rows = {"f1_multicoil_dynamic": run_multicoil_dynamic(nf, torch, dev),
                          "f2_differentiable_spiral": run_differentiable(nf, torch, dev)}
     torch.cuda.synchronize()
@@ -550,7 +560,7 @@ def cpu_baseline(seconds: float = 10.0):
     """The FP64 oracle's forward + adjoint on the full 2D workload, timed on the
     host (plan precompute excluded), repeated until ``seconds`` have elapsed."""
     oracle, spec, plan, x = _oracle_setup()
-    reps, t0 = 0, time.perf_counter()
+    reps, t0, c0 = 0, time.perf_counter(), time.process_time()
     while True:
         y = oracle.forward(plan, x)
         oracle.adjoint(plan, y)
@@ -558,7 +568,8 @@ def cpu_baseline(seconds: float = 10.0):
         el = time.perf_counter() - t0
         if el >= seconds:
             break
-    return {"value": round(spec["M"] * reps / el, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+    cores = max(1, round((time.process_time() - c0) / el))   # threads the timed loop kept busy
+    return {"value": round(spec["M"] * reps / el, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{reps} forward+adjoint pairs on the full radial2d_256 workload (206,336 points), "
                       f"FP64 numpy, plan excluded, {el:.1f} s"}
 
@@ -571,10 +582,11 @@ def reference(args):
     oracle, spec, plan, x = _oracle_setup()
     for _ in range(args.warmup):
         oracle.adjoint(plan, oracle.forward(plan, x))
-    t0 = time.perf_counter()
+    t0, c0 = time.perf_counter(), time.process_time()
     for _ in range(args.steps):
         oracle.adjoint(plan, oracle.forward(plan, x))
     el = time.perf_counter() - t0
+    cores = max(1, round((time.process_time() - c0) / el))   # threads the timed loop kept busy
     value = spec["M"] * args.steps / el
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
@@ -583,7 +595,7 @@ def reference(args):
         "config": {"workload": "radial2d_256: 2D 256x256 image, 512x512 grid, J=6x6, golden-angle radial "
                                "403 spokes x 512 samples (206,336 points), ellipse phantom",
                    "step": "A x then A^H y (forward + adjoint)", "parallelism": "host CPU"},
-        "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{args.steps} timed forward+adjoint pairs on the full workload, FP64 numpy, "
                                    f"plan excluded"},
         "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -600,6 +612,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-solvers", action="store_true", help="skip the solver timings (rows a9)")
+    ap.add_argument("--no-rows", action="store_true",
+                    help="time only the forward+adjoint step (no A^H A, Toeplitz, solver or extension rows)")
     ap.add_argument("--workloads", default="radial2d_256,kooshball3d_128",
                     help="comma list; the first sets value/roofline, the second is reported under 'also'")
     args = ap.parse_args(argv)
