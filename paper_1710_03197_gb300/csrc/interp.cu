@@ -279,8 +279,15 @@ __device__ __forceinline__ void reduce_tile(const float2* __restrict__ tiles, co
   const int gsize = blockDim.x / NG;
   const int h = threadIdx.x / gsize;
   const int tg = threadIdx.x - h * gsize;
+  // A tile with few (neighbour, chunk) pairs is summed by group 0 alone; the
+  // other groups then skip their set-up (CTA-uniform decision).
+  int npairs = 0;
+  for (int e = 0; e < (1 << D); ++e) npairs += s_q1[e] - s_q0[e];
+  const int NGe = npairs > 2 * (1 << D) ? NG : 1;
+  const bool active = h < NGe;
 #pragma unroll
   for (int k = 0; k < CPT; ++k) {
+    acc[k] = make_float2(0.f, 0.f);
     const int c = min(tg + k * gsize, tile_cells - 1);
     int lc[3] = {0, 0, 0};
     if (D == 1) {
@@ -308,24 +315,26 @@ __device__ __forceinline__ void reduce_tile(const float2* __restrict__ tiles, co
 #pragma unroll
     for (int a = 0; a < D; ++a) off += ((bc[a] << g.lT[a]) + lc[a]) * (int)g.Kstride[a];
     goff[k] = off;
-    acc[k] = make_float2(0.f, 0.f);
   }
   const int64_t pc = g.padded_cells;
-  int idx = 0;  // running index over the (e, chunk) pairs
-  for (int e = 0; e < (1 << D); ++e) {
-    const int q0 = s_q0[e], q1 = s_q1[e];
-    const int delta = s_delta[e];
-    // first pair of this e that belongs to group h
-    int q = q0 + ((h - idx) % NG + NG) % NG;
-    for (; q < q1; q += NG) {
-      const float2* src = tiles + (int64_t)q * pc + delta;
+  if (active) {
+    int idx = 0;  // running index over the (e, chunk) pairs
 #pragma unroll
-      for (int k = 0; k < CPT; ++k)
-        if ((emask[k] >> e) & 1u) acc[k] = cadd(acc[k], COHERENT ? __ldcg(&src[loc0[k]]) : __ldg(&src[loc0[k]]));
+    for (int e = 0; e < (1 << D); ++e) {
+      const int q0 = s_q0[e], q1 = s_q1[e];
+      const int delta = s_delta[e];
+      // first pair of this e that belongs to group h
+      int q = q0 + ((h - idx) % NGe + NGe) % NGe;
+      for (; q < q1; q += NGe) {
+        const float2* src = tiles + (int64_t)q * pc + delta;
+#pragma unroll
+        for (int k = 0; k < CPT; ++k)
+          if ((emask[k] >> e) & 1u) acc[k] = cadd(acc[k], COHERENT ? __ldcg(&src[loc0[k]]) : __ldg(&src[loc0[k]]));
+      }
+      idx += q1 - q0;
     }
-    idx += q1 - q0;
   }
-  if (NG > 1) {
+  if (NGe > 1) {
 #pragma unroll
     for (int k = 0; k < CPT; ++k) part[h * (CPT * gsize) + k * gsize + tg] = acc[k];
     __syncthreads();
@@ -333,7 +342,7 @@ __device__ __forceinline__ void reduce_tile(const float2* __restrict__ tiles, co
 #pragma unroll
       for (int k = 0; k < CPT; ++k) {
         float2 t = part[k * gsize + tg];
-        for (int hh = 1; hh < NG; ++hh) t = cadd(t, part[hh * (CPT * gsize) + k * gsize + tg]);
+        for (int hh = 1; hh < NGe; ++hh) t = cadd(t, part[hh * (CPT * gsize) + k * gsize + tg]);
         acc[k] = t;
       }
     }
@@ -361,8 +370,11 @@ k_gridding_reduce(const float2* __restrict__ tiles_b, const int32_t* __restrict_
 // for two dependent global round trips (the permutation, then the samples)
 // instead of one per pass of its warps over the chunk.  The accumulation then
 // follows the same lane layout and bank order as k_gridding_chunk.
-// Shared memory: the split-plane tile, then coef[J0 + J1][cap], y[cap],
-// k[2][cap] (first neighbours relative to the tile origin), cap = chunk size.
+// Shared memory: the split-plane tile, then c0[J0][cap] (row by row: the lanes
+// of a point read one value), c1[cap][J1] (point by point: the J1 lanes of a
+// point read consecutive words, so a warp's 64-bit reads of five points hit
+// distinct bank pairs), y[cap], k[2][cap] (first neighbours relative to the
+// tile origin), cap = chunk size.
 template <int JF>
 __global__ void __launch_bounds__(256, 4)
 k_gridding_chunk_staged(const float2* __restrict__ y_b, float2* __restrict__ tiles_b,
@@ -401,7 +413,7 @@ k_gridding_chunk_staged(const float2* __restrict__ y_b, float2* __restrict__ til
 #pragma unroll
     for (int r = 0; r < (JF > 0 ? JF : kMaxJ); ++r) {
       if (JF == 0 && r >= J1) break;
-      s_c[(J0 + r) * cap + q] = P.coef[P.coef_off[1] + (int64_t)r * P.M + i];
+      s_c[J0 * cap + q * J1 + r] = P.coef[P.coef_off[1] + (int64_t)r * P.M + i];
     }
   }
   if (qs < ch.count) s_y[qs] = __ldg(&y[pm]);
@@ -417,7 +429,7 @@ k_gridding_chunk_staged(const float2* __restrict__ y_b, float2* __restrict__ til
   const int P1 = g.P[1];
   if (sub < per_warp) {
     for (int q = warp * per_warp + sub; q < ch.count; q += nwarps * per_warp) {
-      const float2 yl = cmulc(s_c[(J0 + l) * cap + q], s_y[q]);   // conj(c_last) * y
+      const float2 yl = cmulc(s_c[J0 * cap + q * J1 + l], s_y[q]);   // conj(c_last) * y
       const int ll = s_k[cap + q] + l;
       const int l0 = s_k[q];
 #pragma unroll
