@@ -29,14 +29,16 @@
  * - A plan is not thread-safe: do not call into one plan from two host
  *   threads at once.  Distinct plans are independent.
  * - CUDA graphs: nufft_forward, nufft_adjoint, nufft_selfadjoint, their
- *   host-buffer forms (the kernel part), the stage calls, the batch calls
- *   and solve_cg record their kernel sequence into a CUDA graph on the
- *   second call with the same buffers and stream, and replay it afterwards
- *   (one launch instead of up to a dozen per operator, and hundreds per
- *   solve).  The first call runs eagerly and does any lazy allocation.  When
- *   the stream is already being captured by the caller, the calls launch
- *   normally into the caller's capture.  nufft_set_graphs(plan, 0) turns
- *   recording off.
+ *   host-buffer forms (copies included when both host buffers are
+ *   page-locked; other host memory runs eagerly), the stage calls, the batch and
+ *   multi-coil calls, density compensation, the gridding reconstruction and
+ *   the solvers record their launch sequence into a CUDA graph on the second
+ *   call with the same buffers, parameters and stream, and replay it
+ *   afterwards (one launch instead of up to a dozen per operator, and
+ *   hundreds per solve).  The first call runs eagerly and does any lazy
+ *   allocation.  When the stream is already being captured by the caller,
+ *   the calls launch normally into the caller's capture.
+ *   nufft_set_graphs(plan, 0) turns recording off.
  */
 #ifndef NUFFT_GB300_H
 #define NUFFT_GB300_H

@@ -120,14 +120,34 @@ extern "C" int nufft_selfadjoint(nufft_plan_t* p, const float* x_dev, float* out
   return run_graphed(p, 3, x, out, 0, [&]() { return selfadjoint_impl(p, x, out); });
 }
 
+namespace {
+// Page-locked (cudaHostAlloc / cudaHostRegister) host memory.
+bool page_locked(const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+}  // namespace
+
 extern "C" int nufft_forward_host(nufft_plan_t* p, const float* x_host, float* y_host) {
   TRY(check_plan(p));
   TRY(check_ptr(p, x_host, p->Nprod, "x_host"));
   TRY(check_ptr(p, y_host, p->M, "y_host"));
-  NUFFT_CUDA_TRY(p, cudaMemcpyAsync(p->x_stage, x_host, p->Nprod * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
-  TRY(run_graphed(p, 1, p->x_stage, p->y_stage, 0, [&]() { return forward_impl(p, p->x_stage, p->y_stage); }));
-  if (p->M > 0)
-    NUFFT_CUDA_TRY(p, cudaMemcpyAsync(y_host, p->y_stage, p->M * sizeof(float2), cudaMemcpyDeviceToHost, p->stream));
+  auto body = [&]() -> int {
+    NUFFT_CUDA_TRY(p, cudaMemcpyAsync(p->x_stage, x_host, p->Nprod * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
+    TRY(forward_impl(p, p->x_stage, p->y_stage));
+    if (p->M > 0)
+      NUFFT_CUDA_TRY(p, cudaMemcpyAsync(y_host, p->y_stage, p->M * sizeof(float2), cudaMemcpyDeviceToHost, p->stream));
+    return NUFFT_OK;
+  };
+  // With page-locked buffers the copies are recorded with the kernels (one
+  // graph per buffer pair); other host memory runs eagerly, so a recorded copy
+  // never targets memory that is no longer page-locked.
+  if (page_locked(x_host) && (p->M == 0 || page_locked(y_host))) TRY(run_graphed(p, 21, x_host, y_host, 0, body));
+  else TRY(body());
   NUFFT_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
   return NUFFT_OK;
 }
@@ -136,10 +156,15 @@ extern "C" int nufft_adjoint_host(nufft_plan_t* p, const float* y_host, float* x
   TRY(check_plan(p));
   TRY(check_ptr(p, y_host, p->M, "y_host"));
   TRY(check_ptr(p, x_host, p->Nprod, "x_host"));
-  if (p->M > 0)
-    NUFFT_CUDA_TRY(p, cudaMemcpyAsync(p->y_stage, y_host, p->M * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
-  TRY(run_graphed(p, 2, p->y_stage, p->x_stage, 0, [&]() { return adjoint_impl(p, p->y_stage, p->x_stage); }));
-  NUFFT_CUDA_TRY(p, cudaMemcpyAsync(x_host, p->x_stage, p->Nprod * sizeof(float2), cudaMemcpyDeviceToHost, p->stream));
+  auto body = [&]() -> int {
+    if (p->M > 0)
+      NUFFT_CUDA_TRY(p, cudaMemcpyAsync(p->y_stage, y_host, p->M * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
+    TRY(adjoint_impl(p, p->y_stage, p->x_stage));
+    NUFFT_CUDA_TRY(p, cudaMemcpyAsync(x_host, p->x_stage, p->Nprod * sizeof(float2), cudaMemcpyDeviceToHost, p->stream));
+    return NUFFT_OK;
+  };
+  if (page_locked(x_host) && (p->M == 0 || page_locked(y_host))) TRY(run_graphed(p, 22, y_host, x_host, 0, body));
+  else TRY(body());
   NUFFT_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
   return NUFFT_OK;
 }

@@ -180,3 +180,24 @@ def test_solver_and_recon_replays_match_eager(nf):
             torch.cuda.synchronize()
             assert rel(w.cpu().numpy(), w_eager) < 1e-5
     assert rel(eager["ols_a"], eager["ols_b"]) > 1e-3     # lambda matters, so the key must carry it
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffer_calls_replay_with_new_contents(nf, pinned):
+    """Host-buffer forms: with page-locked buffers the copies are recorded in
+    the graph, so replays must read the buffers' current contents and write
+    the results back; pageable buffers run eagerly."""
+    Nd, Kd, Jd, om, ref = _case()
+    plan = nf.NufftPlan(dev(om), Nd, Kd, Jd)
+    x_h = torch.empty(Nd, dtype=torch.complex64, pin_memory=pinned)
+    y_h = torch.empty(om.shape[0], dtype=torch.complex64, pin_memory=pinned)
+    xo_h = torch.empty(Nd, dtype=torch.complex64, pin_memory=pinned)
+    for it in range(4):                          # eager, record, replay, replay
+        x = cn(Nd, 100 + it)
+        x_h.copy_(torch.from_numpy(x))
+        plan.forward_host(x_h, y_h)
+        y = y_h.numpy().copy()
+        assert rel(y, oracle.forward(ref, x)) < 2e-5
+        plan.adjoint_host(y_h, xo_h)
+        assert rel(xo_h.numpy(), oracle.adjoint(ref, y)) < 2e-5
+    plan.close()
