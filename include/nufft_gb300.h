@@ -143,9 +143,13 @@ int nufft_adjoint(nufft_plan_t* plan, const float* y_dev, float* x_dev);
  * alias.  No allocation. */
 int nufft_selfadjoint(nufft_plan_t* plan, const float* x_dev, float* out_dev);
 
-/* Host-buffer forms of nufft_forward / nufft_adjoint: copy the input to the
- * plan's device staging buffer, run the operator, copy the result back and
- * synchronize.  Page-locked host memory gives the fastest copies. */
+/* Host-buffer forms of nufft_forward / nufft_adjoint; they return after the
+ * result is in host memory (the plan's stream is synchronized).  With
+ * page-locked host buffers (cudaHostAlloc, cudaHostRegister) the FFT reads or
+ * writes the image in host memory directly and only the k-space samples are
+ * copied; any other host memory is copied through the plan's device staging
+ * buffers.  The buffers must stay valid and, if page-locked, stay page-locked
+ * until the call returns. */
 int nufft_forward_host(nufft_plan_t* plan, const float* x_host, float* y_host);
 int nufft_adjoint_host(nufft_plan_t* plan, const float* y_host, float* x_host);
 

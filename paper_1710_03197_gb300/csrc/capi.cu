@@ -121,14 +121,15 @@ extern "C" int nufft_selfadjoint(nufft_plan_t* p, const float* x_dev, float* out
 }
 
 namespace {
-// Page-locked (cudaHostAlloc / cudaHostRegister) host memory.
-bool page_locked(const void* ptr) {
+// The device address of page-locked (cudaHostAlloc / cudaHostRegister) host
+// memory, or nullptr for any other memory.
+void* device_alias(const void* ptr) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return nullptr;
   }
-  return a.type == cudaMemoryTypeHost;
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 }  // namespace
 
@@ -136,17 +137,26 @@ extern "C" int nufft_forward_host(nufft_plan_t* p, const float* x_host, float* y
   TRY(check_plan(p));
   TRY(check_ptr(p, x_host, p->Nprod, "x_host"));
   TRY(check_ptr(p, y_host, p->M, "y_host"));
+  // Page-locked buffers: the first FFT pass reads the image straight from host
+  // memory, the samples come back by one copy, and the whole sequence is
+  // recorded as one graph per buffer pair.  Other host memory goes through the
+  // staging buffers eagerly, so a recorded access never meets memory that is
+  // no longer page-locked (checked on every call).
+  const float2* x_alias = static_cast<const float2*>(device_alias(x_host));
+  const bool locked = x_alias && (p->M == 0 || device_alias(y_host));
   auto body = [&]() -> int {
-    NUFFT_CUDA_TRY(p, cudaMemcpyAsync(p->x_stage, x_host, p->Nprod * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
-    TRY(forward_impl(p, p->x_stage, p->y_stage));
+    const float2* x = x_alias;
+    if (!locked) {
+      NUFFT_CUDA_TRY(p, cudaMemcpyAsync(p->x_stage, x_host, p->Nprod * sizeof(float2), cudaMemcpyHostToDevice,
+                                        p->stream));
+      x = p->x_stage;
+    }
+    TRY(forward_impl(p, x, p->y_stage));
     if (p->M > 0)
       NUFFT_CUDA_TRY(p, cudaMemcpyAsync(y_host, p->y_stage, p->M * sizeof(float2), cudaMemcpyDeviceToHost, p->stream));
     return NUFFT_OK;
   };
-  // With page-locked buffers the copies are recorded with the kernels (one
-  // graph per buffer pair); other host memory runs eagerly, so a recorded copy
-  // never targets memory that is no longer page-locked.
-  if (page_locked(x_host) && (p->M == 0 || page_locked(y_host))) TRY(run_graphed(p, 21, x_host, y_host, 0, body));
+  if (locked) TRY(run_graphed(p, 21, x_host, y_host, 0, body));
   else TRY(body());
   NUFFT_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
   return NUFFT_OK;
@@ -156,14 +166,19 @@ extern "C" int nufft_adjoint_host(nufft_plan_t* p, const float* y_host, float* x
   TRY(check_plan(p));
   TRY(check_ptr(p, y_host, p->M, "y_host"));
   TRY(check_ptr(p, x_host, p->Nprod, "x_host"));
+  // Page-locked buffers: the samples go up by one copy and the last inverse
+  // FFT pass writes the image straight to host memory (see the forward form).
+  float2* x_alias = static_cast<float2*>(device_alias(x_host));
+  const bool locked = x_alias && (p->M == 0 || device_alias(y_host));
   auto body = [&]() -> int {
     if (p->M > 0)
       NUFFT_CUDA_TRY(p, cudaMemcpyAsync(p->y_stage, y_host, p->M * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
+    if (locked) return adjoint_impl(p, p->y_stage, x_alias);
     TRY(adjoint_impl(p, p->y_stage, p->x_stage));
     NUFFT_CUDA_TRY(p, cudaMemcpyAsync(x_host, p->x_stage, p->Nprod * sizeof(float2), cudaMemcpyDeviceToHost, p->stream));
     return NUFFT_OK;
   };
-  if (page_locked(x_host) && (p->M == 0 || page_locked(y_host))) TRY(run_graphed(p, 22, y_host, x_host, 0, body));
+  if (locked) TRY(run_graphed(p, 22, y_host, x_host, 0, body));
   else TRY(body());
   NUFFT_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
   return NUFFT_OK;
