@@ -112,7 +112,10 @@ struct nufft_plan {
   double2* Tinv;            // J_i x J_i min-max inverses, dim i at T_off[i]
   int64_t T_off[nufft::kMaxDim];
   float* om_sorted;         // [d][M] trajectory in tile-sorted order
+  double2* cheb;            // Chebyshev expansions of the coefficients in the offset (plan.cu)
+  int cheb_ok[2];           // expansion used for the coefficients / their derivatives
   float2* dcoef;            // [sum_i J_i][M] d coef / d omega (allocated on first use)
+
 
   // Toeplitz-embedded normal operator (nufft_toeplitz_init)
   nufft_plan* toep_geom;    // FFT geometry N in a 2N grid, no trajectory

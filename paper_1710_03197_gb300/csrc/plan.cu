@@ -281,31 +281,18 @@ __global__ void k_bin_start(const uint32_t* key, int64_t M, int64_t nbins, int32
   bin_start[b] = (int32_t)lo;
 }
 
-// Per sorted point and dimension: first neighbour and the J min-max coefficients.
-// With deriv = 1 the same kernel writes d c / d w = T d r / d w instead, where
-// d r_j / d w = sum_n s_n (-i t_n) exp(-i theta t_n) (the neighbourhood fixed):
-// the summand gains the factor -i t_n.  om_sorted = 1: om is [d][M] in sorted
-// order; otherwise om is the caller's M x d array and perm maps to it, and the
-// sorted copy is written to om_out (if not NULL).
-__global__ void k_coefficients(const float* om, int om_sorted, Geom g, int64_t M, const int32_t* perm,
-                               const double* s64, DimTables D, const double2* Tinv, int32_t* kf_out, float2* coef,
-                               int64_t coef_off0, int64_t coef_off1, int64_t coef_off2, int deriv, float* om_out) {
-  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= M * g.d) return;
-  const int a = (int)(idx / M);
-  const int64_t i = idx - (int64_t)a * M;
-  const int N = g.N[a], K = g.K[a], J = g.J[a];
-  const float wf = om_sorted ? om[(int64_t)a * M + i] : om[(int64_t)perm[i] * g.d + a];
-  if (om_out) om_out[(int64_t)a * M + i] = wf;
-  const double w = (double)wf;
-  const double k0 = offset_k0(w, K, J);
+// The J min-max coefficients of one dimension (or, deriv = 1, their
+// derivatives d c / d w with the neighbourhood fixed) for the offsets
+// theta_j = w - gamma (k0 + j) = theta_1 - gamma (j - 1), j = 1..J:
+//   r_j = sum_n s_n exp(-i theta_j t_n),  c = T r  (T = G^{-1}),
+// and for the derivative the summand gains the factor -i t_n.  The sum runs
+// with the rotation exp(-i theta) from its value at n = 0 (t = -N/2).
+__device__ void minmax_coefs(double theta1, int N, int K, int J, const double* s, const double2* T, int deriv,
+                             double2* c) {
   const double gamma = (2.0 * kPi) / K;
-  const double* s = s64 + D.s_off[a];
   double2 r[kMaxJ];
   for (int j = 1; j <= J; ++j) {
-    // r_j = sum_n s_n exp(-i theta t_n), theta = w - gamma (k0 + j), t_n = n - N/2,
-    // accumulated with the rotation exp(-i theta) from exp(+i theta N/2).
-    const double theta = w - gamma * (k0 + (double)j);
+    const double theta = theta1 - gamma * (double)(j - 1);
     double sn, cs;
     sincos(-theta, &sn, &cs);            // rotation per step
     double es, ec;
@@ -327,8 +314,6 @@ __global__ void k_coefficients(const float* om, int om_sorted, Geom g, int64_t M
     }
     r[j - 1] = make_double2(re, im);
   }
-  const double2* T = Tinv + D.T_off[a];
-  const int64_t off = a == 0 ? coef_off0 : (a == 1 ? coef_off1 : coef_off2);
   for (int j = 0; j < J; ++j) {
     double re = 0.0, im = 0.0;
     for (int q = 0; q < J; ++q) {
@@ -336,7 +321,122 @@ __global__ void k_coefficients(const float* om, int om_sorted, Geom g, int64_t M
       re += t.x * r[q].x - t.y * r[q].y;
       im += t.x * r[q].y + t.y * r[q].x;
     }
-    coef[off + (int64_t)j * M + i] = make_float2((float)re, (float)im);
+    c[j] = make_double2(re, im);
+  }
+}
+
+// The coefficients depend on w only through the fractional offset
+// delta = w / gamma - k0 - J/2 in [0, 1): theta_1 = gamma (delta + J/2 - 1).
+// So per dimension they are smooth functions of one variable on [0, 1], and
+// the plan expands each in Chebyshev polynomials of x = 2 delta - 1 (kCheb
+// terms, coefficients from the values at the Chebyshev nodes), then evaluates
+// the expansions per point (Clenshaw, FP64) instead of the N-term sums.  The
+// expansion is checked against the sums at other points of [0, 1] and used
+// only where it agrees to kChebTol relative to the largest coefficient.
+constexpr int kCheb = 24;
+constexpr double kChebTol = 1e-10;
+
+__device__ __forceinline__ double cheb_node(int m) { return cos(kPi * (m + 0.5) / kCheb); }
+
+// table layout: [(a * 2 + deriv) * kMaxJ + j] * kCheb + k
+__global__ void k_cheb_fit(DimTables D, const double* s64, const double2* Tinv, double2* table) {
+  const int a = blockIdx.x >> 1, deriv = blockIdx.x & 1;
+  __shared__ double2 vals[kCheb][kMaxJ];
+  const int N = D.N[a], K = D.K[a], J = D.J[a];
+  const double gamma = (2.0 * kPi) / K;
+  for (int m = threadIdx.x; m < kCheb; m += blockDim.x) {
+    const double delta = 0.5 * (cheb_node(m) + 1.0);
+    double2 c[kMaxJ];
+    minmax_coefs(gamma * (delta + 0.5 * J - 1.0), N, K, J, s64 + D.s_off[a], Tinv + D.T_off[a], deriv, c);
+    for (int j = 0; j < J; ++j) vals[m][j] = c[j];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < J * kCheb; t += blockDim.x) {
+    const int j = t / kCheb, k = t - j * kCheb;
+    double re = 0.0, im = 0.0;
+    for (int m = 0; m < kCheb; ++m) {
+      const double w = cos(kPi * k * (m + 0.5) / kCheb);
+      re += w * vals[m][j].x;
+      im += w * vals[m][j].y;
+    }
+    const double f = (k == 0 ? 1.0 : 2.0) / kCheb;
+    table[((a * 2 + deriv) * kMaxJ + j) * kCheb + k] = make_double2(f * re, f * im);
+  }
+}
+
+__device__ __forceinline__ double2 cheb_eval(const double2* a, double x) {
+  double2 b1 = make_double2(0.0, 0.0), b2 = make_double2(0.0, 0.0);
+  for (int k = kCheb - 1; k >= 1; --k) {
+    const double2 b0 = make_double2(a[k].x + 2.0 * x * b1.x - b2.x, a[k].y + 2.0 * x * b1.y - b2.y);
+    b2 = b1;
+    b1 = b0;
+  }
+  return make_double2(a[0].x + x * b1.x - b2.x, a[0].y + x * b1.y - b2.y);
+}
+
+// Largest deviation of the expansion from the sums at kChebCheck points per
+// (dimension, deriv), relative to the largest coefficient there; one block
+// per (dimension, deriv), written to err[a * 2 + deriv].
+constexpr int kChebCheck = 61;
+__global__ void k_cheb_check(DimTables D, const double* s64, const double2* Tinv, const double2* table, double* err) {
+  const int a = blockIdx.x >> 1, deriv = blockIdx.x & 1;
+  const int N = D.N[a], K = D.K[a], J = D.J[a];
+  const double gamma = (2.0 * kPi) / K;
+  __shared__ double s_err[256], s_max[256];
+  double e = 0.0, mx = 0.0;
+  for (int t = threadIdx.x; t < kChebCheck; t += blockDim.x) {
+    const double delta = (t + 0.5) / kChebCheck;
+    double2 c[kMaxJ];
+    minmax_coefs(gamma * (delta + 0.5 * J - 1.0), N, K, J, s64 + D.s_off[a], Tinv + D.T_off[a], deriv, c);
+    for (int j = 0; j < J; ++j) {
+      const double2 v = cheb_eval(table + ((a * 2 + deriv) * kMaxJ + j) * kCheb, 2.0 * delta - 1.0);
+      e = fmax(e, hypot(v.x - c[j].x, v.y - c[j].y));
+      mx = fmax(mx, hypot(c[j].x, c[j].y));
+    }
+  }
+  s_err[threadIdx.x] = e;
+  s_max[threadIdx.x] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int t = 1; t < (int)blockDim.x; ++t) {
+      e = fmax(e, s_err[t]);
+      mx = fmax(mx, s_max[t]);
+    }
+    err[blockIdx.x] = mx > 0.0 ? e / mx : 0.0;
+  }
+}
+
+// Per sorted point and dimension: first neighbour and the J min-max coefficients
+// (deriv = 1: d c / d w instead).  cheb != NULL evaluates the plan's Chebyshev
+// expansions, else the sums.  om_sorted = 1: om is [d][M] in sorted order;
+// otherwise om is the caller's M x d array and perm maps to it, and the sorted
+// copy is written to om_out (if not NULL).
+__global__ void k_coefficients(const float* om, int om_sorted, Geom g, int64_t M, const int32_t* perm,
+                               const double* s64, DimTables D, const double2* Tinv, int32_t* kf_out, float2* coef,
+                               int64_t coef_off0, int64_t coef_off1, int64_t coef_off2, int deriv, float* om_out,
+                               const double2* cheb) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= M * g.d) return;
+  const int a = (int)(idx / M);
+  const int64_t i = idx - (int64_t)a * M;
+  const int N = g.N[a], K = g.K[a], J = g.J[a];
+  const float wf = om_sorted ? om[(int64_t)a * M + i] : om[(int64_t)perm[i] * g.d + a];
+  if (om_out) om_out[(int64_t)a * M + i] = wf;
+  const double w = (double)wf;
+  const double k0 = offset_k0(w, K, J);
+  const double gamma = (2.0 * kPi) / K;
+  const int64_t off = a == 0 ? coef_off0 : (a == 1 ? coef_off1 : coef_off2);
+  if (cheb) {
+    const double delta = w / gamma - k0 - 0.5 * J;
+    const double x = fmin(1.0, fmax(-1.0, 2.0 * delta - 1.0));
+    for (int j = 0; j < J; ++j) {
+      const double2 v = cheb_eval(cheb + ((a * 2 + deriv) * kMaxJ + j) * kCheb, x);
+      coef[off + (int64_t)j * M + i] = make_float2((float)v.x, (float)v.y);
+    }
+  } else {
+    double2 c[kMaxJ];
+    minmax_coefs(w - gamma * (k0 + 1.0), N, K, J, s64 + D.s_off[a], Tinv + D.T_off[a], deriv, c);
+    for (int j = 0; j < J; ++j) coef[off + (int64_t)j * M + i] = make_float2((float)c[j].x, (float)c[j].y);
   }
   if (kf_out) kf_out[(int64_t)a * M + i] = wrap_first(k0, K);
 }
@@ -423,7 +523,8 @@ cudaError_t dalloc(nufft_plan_t* p, T** ptr, int64_t count) {
 void free_plan_memory(nufft_plan_t* p) {
   void* bufs[] = {p->s, p->twiddle, p->kf, p->coef, p->perm, p->bin_start, p->chunks, p->bin_chunk,
                   p->tiles, p->grid, p->ytmp, p->x_stage, p->y_stage, p->solver_ws, p->kspace_ws, p->mbuf,
-                  p->s64, p->Tinv, p->om_sorted, p->dcoef, p->bgrid, p->btiles, p->bytmp, p->bimg};
+                  p->s64, p->Tinv, p->om_sorted, p->dcoef, p->bgrid, p->btiles, p->bytmp, p->bimg,
+                  p->cheb};
   for (void* b : bufs)
     if (b) cudaFree(b);
 }
@@ -558,10 +659,27 @@ int build_plan(nufft_plan_t* p, const float* om) {
   NUFFT_CUDA_TRY(p, dalloc(p, &p->coef, coef_tot));
   NUFFT_CUDA_TRY(p, dalloc(p, &p->om_sorted, M * d));
   if (M > 0) {
+    // Chebyshev expansions of the coefficients in the offset delta, checked
+    // against the sums (kept for d c / d w too)
+    NUFFT_CUDA_TRY(p, dalloc(p, &p->cheb, (int64_t)d * 2 * kMaxJ * kCheb));
+    double* err = nullptr;
+    NUFFT_CUDA_TRY(p, cudaMalloc((void**)&err, 2 * kMaxDim * sizeof(double)));
+    struct G5 { void* a; ~G5() { if (a) cudaFree(a); } } g5{err};
+    k_cheb_fit<<<2 * d, 64, 0, st>>>(D, s64, Tinv, p->cheb);
+    NUFFT_CUDA_TRY(p, cudaGetLastError());
+    k_cheb_check<<<2 * d, 64, 0, st>>>(D, s64, Tinv, p->cheb, err);
+    NUFFT_CUDA_TRY(p, cudaGetLastError());
+    double herr[2 * kMaxDim];
+    NUFFT_CUDA_TRY(p, cudaMemcpyAsync(herr, err, 2 * d * sizeof(double), cudaMemcpyDeviceToHost, st));
+    NUFFT_CUDA_TRY(p, cudaStreamSynchronize(st));
+    p->cheb_ok[0] = p->cheb_ok[1] = 1;
+    for (int a = 0; a < d; ++a)
+      for (int v = 0; v < 2; ++v)
+        if (!(herr[a * 2 + v] <= kChebTol)) p->cheb_ok[v] = 0;
     const int64_t n = M * d;
     k_coefficients<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(om, 0, g, M, p->perm, s64, D, Tinv, p->kf, p->coef,
                                                                p->coef_off[0], p->coef_off[1], p->coef_off[2], 0,
-                                                               p->om_sorted);
+                                                               p->om_sorted, p->cheb_ok[0] ? p->cheb : nullptr);
     NUFFT_CUDA_TRY(p, cudaGetLastError());
   }
   NUFFT_CUDA_TRY(p, cudaMemcpyAsync(hflag, flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -595,7 +713,7 @@ int ensure_coef_derivatives(nufft_plan_t* p) {
   const int64_t n = p->M * p->g.d;
   k_coefficients<<<(unsigned)((n + 127) / 128), 128, 0, p->stream>>>(
       p->om_sorted, 1, p->g, p->M, p->perm, p->s64, D, p->Tinv, nullptr, p->dcoef, p->coef_off[0], p->coef_off[1],
-      p->coef_off[2], 1, nullptr);
+      p->coef_off[2], 1, nullptr, p->cheb_ok[1] ? p->cheb : nullptr);
   NUFFT_CUDA_TRY(p, cudaGetLastError());
   return NUFFT_OK;
 }

@@ -82,6 +82,23 @@ def test_minmax_coefficients_are_least_squares_solution(N, K, J):
             assert np.linalg.norm(b - A @ (c[m] + dc)) >= e0
 
 
+@pytest.mark.parametrize("N,K,J", [(16, 32, 6), (12, 24, 5), (32, 32, 4)])
+def test_minmax_coefficients_depend_only_on_the_offset(N, K, J):
+    """Shifting w by whole grid steps (gamma) shifts the neighbourhood by the
+    same number of cells and leaves the coefficients unchanged: they depend on
+    w only through delta = w / gamma - k0 - J/2 in [0, 1), so one smooth
+    function of delta per dimension describes every point."""
+    gamma = 2 * math.pi / K
+    base = np.array([-2.9, -1.234, 0.0, 0.05, 1.0 / 3.0, 1.7])
+    k0, c, _ = oracle.minmax_coefficients_1d(base, N, K, J)
+    delta = base / gamma - k0 - J / 2
+    assert np.all((delta >= 0) & (delta < 1))
+    for shift in (1, 3, -5):
+        k1, c1, _ = oracle.minmax_coefficients_1d(base + shift * gamma, N, K, J)
+        np.testing.assert_array_equal(k1, k0 + shift)
+        np.testing.assert_allclose(c1, c, rtol=0, atol=1e-10 * np.abs(c).max())
+
+
 def test_separable_coefficients_solve_the_2d_minmax_problem():
     """The Kronecker product of 1D solutions is the 2D least-squares solution."""
     Nd, Kd, Jd = (8, 10), (16, 20), (4, 5)
