@@ -452,10 +452,24 @@ __global__ void k_coefficients(const float* om, int om_sorted, Geom g, int64_t M
 // per chunk buckets the points by b and forms the groups greedily, taking
 // from the fullest bucket whose window is still free (a conflicting point
 // only when no free window is left); stable and deterministic.
-__global__ void k_bank_order(const float* om, Geom g, const Chunk* chunks, int64_t nchunks, const int32_t* perm_in,
-                             int32_t* perm_out, int32_t* next) {
-  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (c >= nchunks) return;
+// One warp per chunk: the lanes compute the points' start banks b, lane k
+// keeps bucket k (its count, and its points in chunk order in shared
+// memory), and each greedy step is a warp-wide arg-max (fullest bucket whose
+// window is free, lowest b on ties), so the order equals the one-thread
+// greedy described above.  Shared memory per warp: b[cap] (bytes),
+// ord[cap] and out[cap] (16-bit chunk positions), cap = chunk size (<= 2^15).
+constexpr int kBankWarps = 4;
+
+__global__ void __launch_bounds__(32 * kBankWarps)
+k_bank_order(const float* om, Geom g, const Chunk* chunks, int64_t nchunks, const int32_t* perm_in,
+             int32_t* perm_out, int cap) {
+  extern __shared__ unsigned char sbank[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t c = blockIdx.x * (int64_t)kBankWarps + w;
+  if (c >= nchunks) return;   // warp-uniform; only warp-level synchronisation below
+  unsigned char* s_b = sbank + (size_t)w * cap * 5;
+  int16_t* s_ord = reinterpret_cast<int16_t*>(s_b + cap);
+  int16_t* s_out = s_ord + cap;
   const Chunk ch = chunks[c];
   const int d = g.d;
   const int JL = g.J[d - 1];
@@ -469,43 +483,53 @@ __global__ void k_bank_order(const float* om, Geom g, const Chunk* chunks, int64
       rem /= g.nb[a];
     }
   }
-  int head[32], tail[32], cnt[32];
-  for (int k = 0; k < 32; ++k) { head[k] = -1; tail[k] = -1; cnt[k] = 0; }
-  for (int q = 0; q < ch.count; ++q) {
-    const int64_t i = (int64_t)ch.start + q;
-    const int64_t m = perm_in[i];
+  for (int q = lane; q < ch.count; q += 32) {
+    const int64_t m = perm_in[(int64_t)ch.start + q];
     int cell = 0;
     for (int a = 0; a < d; ++a) {
       const int kf = wrap_first(offset_k0((double)om[m * d + a], g.K[a], g.J[a]), g.K[a]);
       cell = cell * g.P[a] + (kf - org[a]);
     }
-    const int b = cell & 31;
-    next[i] = -1;
-    if (tail[b] >= 0) next[(int64_t)ch.start + tail[b]] = q; else head[b] = q;
-    tail[b] = q;
-    ++cnt[b];
+    s_b[q] = (unsigned char)(cell & 31);
   }
+  __syncwarp();
+  int cnt = 0;
+  for (int q = 0; q < ch.count; ++q) cnt += s_b[q] == lane;
+  int first = cnt;                                     // exclusive prefix over the lanes
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, first, o);
+    if (lane >= o) first += v;
+  }
+  first -= cnt;
+  for (int q = 0, pos = first; q < ch.count; ++q)
+    if (s_b[q] == lane) s_ord[pos++] = (int16_t)q;
+  __syncwarp();
+  const unsigned my_win = (base_mask << lane) | (lane ? (base_mask >> (32 - lane)) : 0u);
+  int head = first;
   int out = 0;
   while (out < ch.count) {
     unsigned used = 0u;
     for (int s = 0; s < G && out < ch.count; ++s) {
-      int best = -1;
-      for (int k = 0; k < 32; ++k) {
-        if (cnt[k] == 0) continue;
-        const unsigned win = (base_mask << k) | (k ? (base_mask >> (32 - k)) : 0u);
-        if ((win & used) == 0u && (best < 0 || cnt[k] > cnt[best])) best = k;
+      // key: count + 1 in the high bits, 31 - lane low (ties -> lowest lane)
+      const unsigned free_key = (cnt > 0 && (my_win & used) == 0u) ? ((unsigned)(cnt + 1) << 5) | (31u - lane) : 0u;
+      unsigned best_key = __reduce_max_sync(0xffffffffu, free_key);
+      if (best_key == 0u)
+        best_key = __reduce_max_sync(0xffffffffu, cnt > 0 ? ((unsigned)(cnt + 1) << 5) | (31u - lane) : 0u);
+      const int best = 31 - (int)(best_key & 31u);
+      int q = 0;
+      if (lane == best) {
+        q = s_ord[head++];
+        --cnt;
       }
-      if (best < 0)
-        for (int k = 0; k < 32; ++k)
-          if (cnt[k] > 0 && (best < 0 || cnt[k] > cnt[best])) best = k;
-      const int q = head[best];
-      head[best] = next[(int64_t)ch.start + q];
-      --cnt[best];
+      q = __shfl_sync(0xffffffffu, q, best);
       used |= (base_mask << best) | (best ? (base_mask >> (32 - best)) : 0u);
-      perm_out[(int64_t)ch.start + out] = perm_in[(int64_t)ch.start + q];
+      if (lane == 0) s_out[out] = (int16_t)q;
       ++out;
     }
   }
+  __syncwarp();
+  for (int o = lane; o < ch.count; o += 32)
+    perm_out[(int64_t)ch.start + o] = perm_in[(int64_t)ch.start + s_out[o]];
 }
 
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
@@ -641,12 +665,17 @@ int build_plan(nufft_plan_t* p, const float* om) {
 
   // ---- order the points of each chunk for conflict-free shared-memory atomics
   if (M > 0 && p->nchunks > 0) {
-    int32_t *perm2 = nullptr, *nxt = nullptr;
+    int32_t* perm2 = nullptr;
     NUFFT_CUDA_TRY(p, cudaMalloc((void**)&perm2, M * sizeof(int32_t)));
     struct G2 { void* a; ~G2() { if (a) cudaFree(a); } } g2{perm2};
-    NUFFT_CUDA_TRY(p, cudaMalloc((void**)&nxt, M * sizeof(int32_t)));
-    struct G3 { void* a; ~G3() { if (a) cudaFree(a); } } g3{nxt};
-    k_bank_order<<<(unsigned)((p->nchunks + 63) / 64), 64, 0, st>>>(om, g, p->chunks, p->nchunks, p->perm, perm2, nxt);
+    const int cap = kChunkPoints[d];
+    static_assert(kChunkPoints[1] < 32768 && kChunkPoints[2] < 32768 && kChunkPoints[3] < 32768,
+                  "16-bit chunk positions");
+    const size_t smem = (size_t)kBankWarps * cap * 5;
+    if (smem > 48 * 1024)
+      NUFFT_CUDA_TRY(p, cudaFuncSetAttribute(k_bank_order, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_bank_order<<<(unsigned)((p->nchunks + kBankWarps - 1) / kBankWarps), 32 * kBankWarps, smem, st>>>(
+        om, g, p->chunks, p->nchunks, p->perm, perm2, cap);
     NUFFT_CUDA_TRY(p, cudaGetLastError());
     NUFFT_CUDA_TRY(p, cudaMemcpyAsync(p->perm, perm2, M * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
     NUFFT_CUDA_TRY(p, cudaStreamSynchronize(st));

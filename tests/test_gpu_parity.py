@@ -137,6 +137,24 @@ def test_tile_sort_and_bank_order(case):
             loc_s = kf[stable[c0:c1]] - tile
             cell_s = np.ravel_multi_index(tuple(loc_s.T), P) & 31
             plain = sum(mult(cell_s[g:g + G]) for g in range(0, len(cell_s), G))
+            # exactly the greedy: per group of G, take from the fullest bucket
+            # (bank b) whose window [b, b + J_last) is free, lowest b on ties,
+            # else the fullest bucket; each bucket in chunk (stable) order
+            buckets = [[q for q in range(c1 - c0) if cell_s[q] == b] for b in range(32)]
+            want = []
+            while len(want) < c1 - c0:
+                used = 0
+                for _ in range(G):
+                    if len(want) == c1 - c0:
+                        break
+                    def win(b):
+                        return sum(1 << ((b + j) % 32) for j in range(JL))
+                    free = [b for b in range(32) if buckets[b] and not (win(b) & used)]
+                    pool = free or [b for b in range(32) if buckets[b]]
+                    best = max(pool, key=lambda b: (len(buckets[b]), -b))
+                    want.append(stable[c0 + buckets[best].pop(0)])
+                    used |= win(best)
+            np.testing.assert_array_equal(perm[c0:c1], want)
             tot_got += got
             tot_plain += plain
         b0 = b1
