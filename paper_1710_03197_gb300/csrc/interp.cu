@@ -325,23 +325,28 @@ __device__ __forceinline__ void reduce_tile(const float2* __restrict__ tiles, co
       const int delta = s_delta[e];
       // first pair of this e that belongs to group h
       int q = q0 + ((h - idx) % NGe + NGe) % NGe;
-      // two pairs per step: both pairs' loads are in flight before the adds,
-      // which keep the pair order (acc + v(q) + v(q + NGe))
-      for (; q + NGe < q1; q += 2 * NGe) {
-        const float2* src0 = tiles + (int64_t)q * pc + delta;
-        const float2* src1 = src0 + (int64_t)NGe * pc;
-        float2 v0[CPT], v1[CPT];
+      // DEPTH pairs per step: all their loads are in flight before the adds,
+      // which keep the pair order (acc + v(q) + v(q + NGe) + ...)
+      constexpr int DEPTH = 2;
+      for (; q + (DEPTH - 1) * NGe < q1; q += DEPTH * NGe) {
+        float2 v[DEPTH][CPT];
 #pragma unroll
-        for (int k = 0; k < CPT; ++k) {
-          const bool on = (emask[k] >> e) & 1u;
-          v0[k] = on ? (COHERENT ? __ldcg(&src0[loc0[k]]) : __ldg(&src0[loc0[k]])) : make_float2(0.f, 0.f);
-          v1[k] = on ? (COHERENT ? __ldcg(&src1[loc0[k]]) : __ldg(&src1[loc0[k]])) : make_float2(0.f, 0.f);
+        for (int u = 0; u < DEPTH; ++u) {
+          const float2* src = tiles + (int64_t)(q + u * NGe) * pc + delta;
+#pragma unroll
+          for (int k = 0; k < CPT; ++k) {
+            const bool on = (emask[k] >> e) & 1u;
+            v[u][k] = on ? (COHERENT ? __ldcg(&src[loc0[k]]) : __ldg(&src[loc0[k]])) : make_float2(0.f, 0.f);
+          }
         }
 #pragma unroll
         for (int k = 0; k < CPT; ++k)
-          if ((emask[k] >> e) & 1u) acc[k] = cadd(cadd(acc[k], v0[k]), v1[k]);
+          if ((emask[k] >> e) & 1u) {
+#pragma unroll
+            for (int u = 0; u < DEPTH; ++u) acc[k] = cadd(acc[k], v[u][k]);
+          }
       }
-      if (q < q1) {
+      for (; q < q1; q += NGe) {
         const float2* src = tiles + (int64_t)q * pc + delta;
 #pragma unroll
         for (int k = 0; k < CPT; ++k)

@@ -33,21 +33,21 @@ constexpr int kDotThreads = 256;
 constexpr int kEwThreads = 256;
 
 // scalar slots in device memory
-enum { S_RR0 = 0, S_RR1 = 1, S_PQ = 2, S_NSLOTS = 8 };
+enum { S_RR0 = 0, S_RR1 = 1, S_NSLOTS = 8 };
 
 enum { V_B = 0, V_R, V_P, V_Q, V_AHY, V_AHYK, V_RHS, V_T, V_DF, V_BF, V_C1, V_C2, V_D0, V_B0 = V_D0 + 3,
        V_COUNT = V_B0 + 3 };
 
 struct Ws {
   float2* v[V_COUNT];
-  double* part;   // [kDotBlocks]
+  double* part;   // [2][kDotBlocks]: per-CTA partial sums (two sets in flight)
   double* sc;     // [S_NSLOTS]
 };
 
 int get_ws(nufft_plan_t* p, Ws* w) {
   const int64_t n = p->Nprod;
   const int64_t vec_bytes = ((n * (int64_t)sizeof(float2) + 255) / 256) * 256;
-  const int64_t bytes = vec_bytes * V_COUNT + (int64_t)(kDotBlocks + S_NSLOTS) * sizeof(double);
+  const int64_t bytes = vec_bytes * V_COUNT + (int64_t)(2 * kDotBlocks + S_NSLOTS) * sizeof(double);
   if (!p->solver_ws) {
     cudaError_t e = cudaMalloc(&p->solver_ws, bytes);
     if (e != cudaSuccess) { p->solver_ws = nullptr; return cuda_check(p, e, "solver work space"); }
@@ -57,7 +57,7 @@ int get_ws(nufft_plan_t* p, Ws* w) {
   char* base = (char*)p->solver_ws;
   for (int i = 0; i < V_COUNT; ++i) w->v[i] = (float2*)(base + vec_bytes * i);
   w->part = (double*)(base + vec_bytes * V_COUNT);
-  w->sc = w->part + kDotBlocks;
+  w->sc = w->part + 2 * kDotBlocks;
   return NUFFT_OK;
 }
 
@@ -94,11 +94,22 @@ __global__ void __launch_bounds__(kDotThreads) k_dot_final(const double* part, d
 // --------------------------------------------------------------- CG vector steps
 __device__ __forceinline__ double safe_div(double a, double b) { return b != 0.0 ? a / b : 0.0; }
 
-// x += alpha p, r -= alpha q, alpha = rr / <p, q>; also the partial sums of <r, r>.
+// Sum of the kDotBlocks partial sums, in the same order in every CTA (so
+// every CTA of a kernel gets the same value).
+__device__ __forceinline__ double sum_partials(const double* part) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < kDotBlocks; i += kDotThreads) s += part[i];
+  const double t = block_sum(s);
+  __syncthreads();   // block_sum's scratch is reused by the caller
+  return t;
+}
+
+// x += alpha p, r -= alpha q, alpha = rr / <p, q> (<p, q> summed here from its
+// partials); also the partial sums of <r, r>.
 __global__ void __launch_bounds__(kDotThreads)
 k_cg_xr(float2* x, float2* r, const float2* p, const float2* q, int64_t n, const double* sc, int rr_slot,
-        double* part) {
-  const float alpha = (float)safe_div(sc[rr_slot], sc[S_PQ]);
+        const double* part_pq, double* part) {
+  const float alpha = (float)safe_div(sc[rr_slot], sum_partials(part_pq));
   double s = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < n; i += (int64_t)kDotBlocks * kDotThreads) {
     const float2 pv = p[i], qv = q[i];
@@ -115,9 +126,13 @@ k_cg_xr(float2* x, float2* r, const float2* p, const float2* q, int64_t n, const
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-// p = r + beta p, beta = rr_new / rr_old
-__global__ void k_cg_p(float2* p, const float2* r, int64_t n, const double* sc, int new_slot, int old_slot) {
-  const float beta = (float)safe_div(sc[new_slot], sc[old_slot]);
+// p = r + beta p, beta = rr_new / rr_old, rr_new summed here from its
+// partials and kept in sc[new_slot] (by CTA 0) for the next step.
+__global__ void __launch_bounds__(kDotThreads)
+k_cg_p(float2* p, const float2* r, int64_t n, double* sc, int new_slot, int old_slot, const double* part_rr) {
+  const double rr_new = sum_partials(part_rr);
+  const float beta = (float)safe_div(rr_new, sc[old_slot]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) sc[new_slot] = rr_new;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float2 rv = r[i];
     float2 pv = p[i];
@@ -289,19 +304,21 @@ template <class Op>
 int cg_core(nufft_plan_t* p, int64_t n, float2* r, float2* pv, float2* q, double* part, double* sc, Op op,
             const float2* b, float2* x, int iters) {
   cudaStream_t st = p->stream;
+  // part holds two sets of partial sums: <p, q> and <r, r>; the kernels that
+  // need a full sum add the partials themselves (no separate final launch)
+  double* part_pq = part;
+  double* part_rr = part + kDotBlocks;
   TRY(op(x, q));
-  k_cg_init<<<kDotBlocks, kDotThreads, 0, st>>>(r, pv, b, q, n, part);
-  k_dot_final<<<1, kDotThreads, 0, st>>>(part, sc + S_RR0);
+  k_cg_init<<<kDotBlocks, kDotThreads, 0, st>>>(r, pv, b, q, n, part_rr);
+  k_dot_final<<<1, kDotThreads, 0, st>>>(part_rr, sc + S_RR0);
   LAUNCH_CHECK(p, "cg init");
   for (int it = 0; it < iters; ++it) {
     const int cur = (it & 1) ? S_RR1 : S_RR0;
     const int nxt = (it & 1) ? S_RR0 : S_RR1;
     TRY(op(pv, q));
-    k_dot_partial<<<kDotBlocks, kDotThreads, 0, st>>>(pv, q, n, part);
-    k_dot_final<<<1, kDotThreads, 0, st>>>(part, sc + S_PQ);
-    k_cg_xr<<<kDotBlocks, kDotThreads, 0, st>>>(x, r, pv, q, n, sc, cur, part);
-    k_dot_final<<<1, kDotThreads, 0, st>>>(part, sc + nxt);
-    k_cg_p<<<ew_blocks(n), kEwThreads, 0, st>>>(pv, r, n, sc, nxt, cur);
+    k_dot_partial<<<kDotBlocks, kDotThreads, 0, st>>>(pv, q, n, part_pq);
+    k_cg_xr<<<kDotBlocks, kDotThreads, 0, st>>>(x, r, pv, q, n, sc, cur, part_pq, part_rr);
+    k_cg_p<<<kDotBlocks, kDotThreads, 0, st>>>(pv, r, n, sc, nxt, cur, part_rr);
     LAUNCH_CHECK(p, "cg iteration");
   }
   return NUFFT_OK;
