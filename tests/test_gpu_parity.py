@@ -420,6 +420,22 @@ def test_l1tv_ols_radial_within_fp32_envelope(nf, monkeypatch):
 
 # ------------------------------------------------------------------ edge cases
 
+@pytest.mark.parametrize("Nd,Kd,Jd", [((64,), (128,), (16,)), ((32, 32), (64, 64), (12, 12)), ((40,), (64,), (9,))])
+def test_wide_neighbourhoods(nf, Nd, Kd, Jd):
+    """Large J makes G ill-conditioned (the plan's check of its Chebyshev
+    expansion may then fall back to the direct sums); the operator must still
+    match the oracle to the operator tolerance."""
+    d = len(Nd)
+    om = W.uniform_random_om(700 * d, d, seed=71)
+    ref = oracle.make_plan(om, Nd, Kd, Jd)
+    x = cn(Nd, 72)
+    with nf.NufftPlan(to_dev(om), Nd, Kd, Jd) as plan:
+        y = host(plan.forward(to_dev(x)))
+        xa = host(plan.adjoint(to_dev(y)))
+    assert rel(y, oracle.forward(ref, x)) < TOL_OP
+    assert rel(xa, oracle.adjoint(ref, y.astype(np.complex128))) < TOL_OP
+
+
 def test_empty_trajectory(nf):
     with nf.NufftPlan(torch.empty((0, 2), dtype=torch.float32, device=DEV), (16, 16), (32, 32), (6, 6)) as plan:
         y = plan.forward(to_dev(cn((16, 16), 1)))
