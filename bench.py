@@ -165,6 +165,13 @@ def run_workload(nf, torch, name: str, steps: int, warmup: int, dev, flush_bytes
     plan = nf.NufftPlan(om_d, spec["Nd"], spec["Kd"], spec["Jd"])
     torch.cuda.synchronize()
     plan_ms = (time.perf_counter() - t0) * 1e3
+    default_tile = plan.info()["tile_last"]
+    plan.close()
+    # the timed steps use the autotuned plan (tile edge chosen by measurement)
+    t0 = time.perf_counter()
+    plan = nf.NufftPlan(om_d, spec["Nd"], spec["Kd"], spec["Jd"], autotune=True)
+    torch.cuda.synchronize()
+    tuned_ms = (time.perf_counter() - t0) * 1e3
     info = plan.info()
     xd = torch.from_numpy(x).to(dev)
     grid = torch.empty(spec["Kd"], dtype=torch.complex64, device=dev)
@@ -253,7 +260,8 @@ def run_workload(nf, torch, name: str, steps: int, warmup: int, dev, flush_bytes
     torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in evm]
 
-    rows = {"a1_plan_ms": round(plan_ms, 3)}
+    rows = {"a1_plan_ms": round(plan_ms, 3), "a1_plan_tuned_ms": round(tuned_ms, 3),
+            "tile_edge": {"default": default_tile, "tuned": info["tile_last"]}}
     if extra_rows:
         rows.update(_extra_rows(plan, torch, spec, x, xd, xo, noise, steps, flush, stream, dev, solvers))
 
@@ -304,6 +312,21 @@ def _extra_rows(plan, torch, spec, x, xd, xo, noise, steps, flush, stream, dev, 
         e1.synchronize()
         st_.append(e0.elapsed_time(e1))
     rows["f4_selfadjoint_toeplitz_ms"] = round(statistics.mean(st_), 5)
+    # cuFFT (through torch.fft) on the same oversampled grid, for comparison
+    # only: the full unpruned transform, no scaling or padding, L2 flushed
+    gfull = torch.randn(*spec["Kd"], dtype=torch.complex64, device=dev)
+    for key, fn in (("cufft_fft_ms", lambda: torch.fft.fftn(gfull)), ("cufft_ifft_ms", lambda: torch.fft.ifftn(gfull))):
+        fn()
+        t_ = []
+        for k in range(steps):
+            flush.fill_(float(k))
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            t_.append(e0.elapsed_time(e1))
+        rows[key] = round(statistics.mean(t_), 5)
+    del gfull
     if solvers:
         # the reconstruction runs of the paper's solvers on this workload's data
         yd = plan.forward(xd)

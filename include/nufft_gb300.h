@@ -91,6 +91,21 @@ typedef struct nufft_plan nufft_plan_t;
 int nufft_plan(int d, const int* Nd, const int* Kd, const int* Jd, int64_t M,
                const float* om_dev, void* stream, nufft_plan_t** out);
 
+/*
+ * nufft_plan_tuned - nufft_plan with the gridding tile edge chosen by
+ * measurement (the paper has no counterpart: it is a property of this
+ * implementation's bin-tiled V^H).  One plan is built per candidate edge
+ * (1D: 256, 512, 1024; 2D: 8, 16, 32; 3D: 8, 16; each clipped to K, edges
+ * whose padded tile does not fit shared memory skipped), each is timed on a
+ * forward + adjoint pair of zero data on `stream` (CUDA events around five
+ * replays of the recorded calls), and the fastest plan is returned; the
+ * others are destroyed.  Same arguments, results (to rounding) and errors as
+ * nufft_plan; nufft_plan_info [14..15] report the chosen edge.  Takes a few
+ * plan builds' time and synchronizes the stream.
+ */
+int nufft_plan_tuned(int d, const int* Nd, const int* Kd, const int* Jd, int64_t M,
+                     const float* om_dev, void* stream, nufft_plan_t** out);
+
 /* Release every device and host buffer the plan owns.  NULL is a no-op.
  * Synchronizes the plan's stream first. */
 int nufft_plan_destroy(nufft_plan_t* plan);

@@ -35,6 +35,8 @@ _PLAN = ctypes.c_void_p
 _SIGS = {
     "nufft_plan": (_i, [_i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i), _i64, _vp, _vp,
                         ctypes.POINTER(_PLAN)]),
+    "nufft_plan_tuned": (_i, [_i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i), _i64, _vp, _vp,
+                              ctypes.POINTER(_PLAN)]),
     "nufft_plan_destroy": (_i, [_PLAN]),
     "nufft_last_error": (ctypes.c_char_p, [_PLAN]),
     "nufft_set_stream": (_i, [_PLAN, _vp]),

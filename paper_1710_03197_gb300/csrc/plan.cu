@@ -751,8 +751,9 @@ int ensure_coef_derivatives(nufft_plan_t* p) {
 
 using namespace nufft;
 
-extern "C" int nufft_plan(int d, const int* Nd, const int* Kd, const int* Jd, int64_t M, const float* om_dev,
-                          void* stream, nufft_plan_t** out) {
+namespace {
+int create_plan(int d, const int* Nd, const int* Kd, const int* Jd, int64_t M, const float* om_dev, void* stream,
+                int tile_edge, nufft_plan_t** out) {
   if (!out) return set_error(nullptr, NUFFT_EINVAL, "out is NULL");
   *out = nullptr;
   if (d < 1 || d > kMaxDim) return set_error(nullptr, NUFFT_EINVAL, "d = %d, must be 1..3", d);
@@ -762,7 +763,7 @@ extern "C" int nufft_plan(int d, const int* Nd, const int* Kd, const int* Jd, in
   Geom g;
   memset(&g, 0, sizeof(g));
   g.d = d;
-  const int base_tile = d == 1 ? 1024 : 16;
+  const int base_tile = tile_edge > 0 ? tile_edge : (d == 1 ? 1024 : 16);
   for (int a = 0; a < d; ++a) {
     const int N = Nd[a], K = Kd[a], J = Jd[a];
     if (!is_pow2(K) || K < kMinK || K > kMaxK)
@@ -811,6 +812,91 @@ extern "C" int nufft_plan(int d, const int* Nd, const int* Kd, const int* Jd, in
     return rc;
   }
   *out = p;
+  return NUFFT_OK;
+}
+}  // namespace
+
+extern "C" int nufft_plan(int d, const int* Nd, const int* Kd, const int* Jd, int64_t M, const float* om_dev,
+                          void* stream, nufft_plan_t** out) {
+  return create_plan(d, Nd, Kd, Jd, M, om_dev, stream, 0, out);
+}
+
+// Tile-edge autotuner: one plan per candidate edge, each timed on a
+// forward + adjoint pair (recorded graph, replayed kTuneReps times between
+// CUDA events on the caller's stream); the fastest plan is returned and the
+// others are destroyed.  Candidates: 1D 256/512/1024, 2D 8/16/32, 3D 8/16
+// (each clipped to K; edges whose padded tile does not fit are skipped).
+extern "C" int nufft_plan_tuned(int d, const int* Nd, const int* Kd, const int* Jd, int64_t M, const float* om_dev,
+                                void* stream, nufft_plan_t** out) {
+  if (!out) return set_error(nullptr, NUFFT_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (d < 1 || d > kMaxDim) return set_error(nullptr, NUFFT_EINVAL, "d = %d, must be 1..3", d);
+  const int cand1[] = {256, 512, 1024}, cand2[] = {8, 16, 32}, cand3[] = {8, 16};
+  const int* cand = d == 1 ? cand1 : (d == 2 ? cand2 : cand3);
+  const int ncand = d == 3 ? 2 : 3;
+  constexpr int kTuneReps = 5;
+  cudaStream_t st = (cudaStream_t)stream;
+  nufft_plan_t* best = nullptr;
+  float best_ms = 0.f;
+  int last_rc = NUFFT_OK;
+  float2 *xb = nullptr, *yb = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&]() {
+    if (xb) cudaFree(xb);
+    if (yb) cudaFree(yb);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  for (int c = 0; c < ncand; ++c) {
+    nufft_plan_t* p = nullptr;
+    int rc = create_plan(d, Nd, Kd, Jd, M, om_dev, stream, cand[c], &p);
+    if (rc != NUFFT_OK) {   // e.g. a padded tile too large for shared memory
+      last_rc = rc;
+      continue;
+    }
+    if (!xb) {
+      cudaError_t e = cudaMalloc((void**)&xb, p->Nprod * sizeof(float2));
+      if (e == cudaSuccess && p->M > 0) e = cudaMalloc((void**)&yb, p->M * sizeof(float2));
+      if (e == cudaSuccess) e = cudaMemsetAsync(xb, 0, p->Nprod * sizeof(float2), st);
+      if (e == cudaSuccess && yb) e = cudaMemsetAsync(yb, 0, p->M * sizeof(float2), st);
+      if (e == cudaSuccess) e = cudaEventCreate(&e0);
+      if (e == cudaSuccess) e = cudaEventCreate(&e1);
+      if (e != cudaSuccess) {
+        nufft_plan_destroy(p);
+        if (best) nufft_plan_destroy(best);
+        cleanup();
+        cudaGetLastError();
+        return set_error(nullptr, NUFFT_ECUDA, "autotune buffers: %s", cudaGetErrorString(e));
+      }
+    }
+    float ms = 0.f;
+    for (int it = 0; it < 2 + kTuneReps && rc == NUFFT_OK; ++it) {   // eager, record, then timed replays
+      if (it == 2) rc = cuda_check(p, cudaEventRecord(e0, st), "autotune event");
+      if (rc == NUFFT_OK) rc = nufft_forward(p, (const float*)xb, (float*)yb);
+      if (rc == NUFFT_OK) rc = nufft_adjoint(p, (const float*)yb, (float*)xb);
+    }
+    if (rc == NUFFT_OK) rc = cuda_check(p, cudaEventRecord(e1, st), "autotune event");
+    if (rc == NUFFT_OK) rc = cuda_check(p, cudaEventSynchronize(e1), "autotune event");
+    if (rc == NUFFT_OK) rc = cuda_check(p, cudaEventElapsedTime(&ms, e0, e1), "autotune event");
+    drop_graphs(p);   // the recorded graphs point at the scratch buffers
+    if (rc != NUFFT_OK) {
+      set_error(nullptr, rc, "%s", p->err);
+      nufft_plan_destroy(p);
+      if (best) nufft_plan_destroy(best);
+      cleanup();
+      return rc;
+    }
+    if (!best || ms < best_ms) {
+      if (best) nufft_plan_destroy(best);
+      best = p;
+      best_ms = ms;
+    } else {
+      nufft_plan_destroy(p);
+    }
+  }
+  cleanup();
+  if (!best) return last_rc != NUFFT_OK ? last_rc : set_error(nullptr, NUFFT_EINVAL, "no tile edge fits");
+  *out = best;
   return NUFFT_OK;
 }
 

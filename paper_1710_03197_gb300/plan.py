@@ -47,7 +47,7 @@ class NufftPlan:
     size, oversampled grid (powers of two) and neighbours per dimension.
     """
 
-    def __init__(self, om: torch.Tensor, Nd, Kd, Jd, stream=None):
+    def __init__(self, om: torch.Tensor, Nd, Kd, Jd, stream=None, autotune: bool = False):
         if om.dim() == 1:
             om = om[:, None]
         d = len(Nd)
@@ -57,8 +57,8 @@ class NufftPlan:
         om_ptr = _dev_ptr(om.contiguous(), M * d, "om", dtype=torch.float32) if M > 0 else ctypes.c_void_p(0)
         self._om = om
         h = ctypes.c_void_p(0)
-        rc = lib.nufft_plan(d, _c_int_arr(Nd), _c_int_arr(Kd), _c_int_arr(Jd), M, om_ptr,
-                            _stream_ptr(stream), ctypes.byref(h))
+        make = lib.nufft_plan_tuned if autotune else lib.nufft_plan   # autotune: tile edge by measurement
+        rc = make(d, _c_int_arr(Nd), _c_int_arr(Kd), _c_int_arr(Jd), M, om_ptr, _stream_ptr(stream), ctypes.byref(h))
         check(rc, None)
         self._h = h
         self.d, self.M = d, M
@@ -352,6 +352,10 @@ class NufftPlan:
 # ---------------------------------------------------------------- same names as the C ABI
 def nufft_plan(om, Nd, Kd, Jd, stream=None) -> NufftPlan:
     return NufftPlan(om, Nd, Kd, Jd, stream)
+
+
+def nufft_plan_tuned(om, Nd, Kd, Jd, stream=None) -> NufftPlan:
+    return NufftPlan(om, Nd, Kd, Jd, stream, autotune=True)
 
 
 def nufft_forward(plan: NufftPlan, x, y=None):

@@ -510,3 +510,24 @@ def test_runs_on_a_side_stream(nf):
     s.synchronize()
     assert rel(y.cpu().numpy(), oracle.forward(ref, x)) < TOL_OP
     plan.close()
+
+
+@pytest.mark.parametrize("name,Nd,Kd,Jd,gen", [
+    ("2d", (64, 64), (128, 128), (6, 6), lambda: W.radial2d_golden(60, 128)),
+    ("3d", (16, 16, 16), (32, 32, 32), (6, 6, 6), lambda: W.kooshball3d(80, 32)),
+    ("1d", (200,), (512,), (6,), lambda: W.uniform_random_om(3000, 1, seed=73)),
+])
+def test_autotuned_plan_matches_oracle(nf, name, Nd, Kd, Jd, gen):
+    """nufft_plan_tuned picks one of its candidate tile edges and gives the
+    same operators as the default plan."""
+    om = gen()
+    ref = oracle.make_plan(om, Nd, Kd, Jd)
+    x = cn(Nd, 74)
+    yin = cn(om.shape[0], 75)
+    with nf.NufftPlan(to_dev(om), Nd, Kd, Jd, autotune=True) as plan:
+        info = plan.info()
+        edge = {1: (256, 512, 1024), 2: (8, 16, 32), 3: (8, 16)}[len(Nd)]
+        for a, t in zip((0, len(Nd) - 1), ("tile_first", "tile_last")):
+            assert info[t] in [min(e, Kd[a]) for e in edge]
+        assert rel(host(plan.forward(to_dev(x))), oracle.forward(ref, x)) < TOL_OP
+        assert rel(host(plan.adjoint(to_dev(yin))), oracle.adjoint(ref, yin)) < TOL_OP
