@@ -305,6 +305,36 @@ int solve_cg_multicoil(nufft_plan_t* plan, const float* coils_dev, int nc, const
                        int maxiter);
 
 /*
+ * Frame sets - a dynamic series (Section 2.2.3, Eqs. 32-33 per frame): frames
+ * with the same image geometry N^d and their own trajectories (one plan each,
+ * any number of points), sharing the coil maps.
+ *
+ *   nufft_frames_create   the set over plans[0..nframes-1] (distinct plans of
+ *                         equal d and N^d; the set does not own them and they
+ *                         must outlive it); work is ordered on `stream`.
+ *   nufft_frames_selfadjoint_multicoil
+ *                         out_f = sum_i conj(c_i) . A_f^H A_f (c_i . x_f) for
+ *                         every frame f.  x_dev, out_dev: nframes x N^d
+ *                         complex64 (frame-major, may not alias); coils_dev:
+ *                         nc x N^d.  The first call with a buffer set runs
+ *                         eagerly; the second records all frames as concurrent
+ *                         branches of one CUDA graph, replayed afterwards as one
+ *                         launch.  Frame plans may not be used on other streams
+ *                         while a call is in flight.
+ *   nufft_frames_set_stream / nufft_frames_destroy (synchronizes the stream).
+ *
+ * Errors: NUFFT_EINVAL (NULL arguments, nc < 1, mismatched or repeated plans),
+ * NUFFT_ENOMEM, NUFFT_ECUDA; nufft_last_error(NULL) or the frame's plan
+ * describes a failure.
+ */
+typedef struct nufft_frames nufft_frames_t;
+int nufft_frames_create(nufft_plan_t* const* plans, int nframes, void* stream, nufft_frames_t** out);
+int nufft_frames_destroy(nufft_frames_t* frames);
+int nufft_frames_set_stream(nufft_frames_t* frames, void* stream);
+int nufft_frames_selfadjoint_multicoil(nufft_frames_t* frames, const float* coils_dev, int nc, const float* x_dev,
+                                       float* out_dev);
+
+/*
  * Toeplitz-embedded normal operator (Section 2.1.5: the paper precomputes
  * A^H A for its iterative solvers, citing Fessler et al.'s Toeplitz method).
  * A^H A is a convolution with t[D] = sum_m exp(i om_m . D), D in (-N, N)^d;

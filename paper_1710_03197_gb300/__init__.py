@@ -16,6 +16,7 @@ from __future__ import annotations
 from ._lib import lib, LIB_PATH, NufftError, check, symbols_declared
 from .plan import (
     NufftPlan,
+    NufftFrames,
     nufft_plan,
     nufft_plan_tuned,
     nufft_forward,
@@ -49,7 +50,7 @@ from .plan import (
 from .autograd import NufftFunction, nufft_apply
 
 __all__ = [
-    "lib", "LIB_PATH", "NufftError", "check", "symbols_declared", "NufftPlan",
+    "lib", "LIB_PATH", "NufftError", "check", "symbols_declared", "NufftPlan", "NufftFrames",
     "nufft_plan", "nufft_plan_tuned", "nufft_forward", "nufft_adjoint", "nufft_selfadjoint",
     "nufft_forward_host", "nufft_adjoint_host", "nufft_scale_pad_fft", "nufft_interp",
     "nufft_gridding", "nufft_gridding_static", "nufft_ifft_crop_rescale", "solve_cg", "solve_l1tv_ols", "solve_l1tv_lad",

@@ -63,6 +63,10 @@ _SIGS = {
     "nufft_adjoint_multicoil": (_i, [_PLAN, _vp, _i, _vp, _vp]),
     "nufft_selfadjoint_multicoil": (_i, [_PLAN, _vp, _i, _vp, _vp]),
     "solve_cg_multicoil": (_i, [_PLAN, _vp, _i, _vp, _vp, _i]),
+    "nufft_frames_create": (_i, [ctypes.POINTER(_PLAN), _i, _vp, ctypes.POINTER(_vp)]),
+    "nufft_frames_destroy": (_i, [_vp]),
+    "nufft_frames_set_stream": (_i, [_vp, _vp]),
+    "nufft_frames_selfadjoint_multicoil": (_i, [_vp, _vp, _i, _vp, _vp]),
     "nufft_trajectory_gradient": (_i, [_PLAN, _vp, _vp, _vp]),
     "nufft_forward_batch": (_i, [_PLAN, _i, _vp, _vp]),
     "nufft_adjoint_batch": (_i, [_PLAN, _i, _vp, _vp]),

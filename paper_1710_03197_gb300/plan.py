@@ -349,6 +349,56 @@ class NufftPlan:
         return x
 
 
+class NufftFrames:
+    """A dynamic series (C: ``nufft_frames_create``): plans of equal image size
+    over per-frame trajectories; the multi-coil normal operator of all frames
+    is recorded as one CUDA graph with the frames as concurrent branches.  The
+    plans must outlive the set."""
+
+    def __init__(self, plans, stream=None):
+        if not plans:
+            raise ValueError("at least one plan")
+        self.plans = list(plans)
+        self.Nd = self.plans[0].Nd
+        self.device = self.plans[0].device
+        arr = (ctypes.c_void_p * len(self.plans))(*[p.handle.value for p in self.plans])
+        h = ctypes.c_void_p(0)
+        check(lib.nufft_frames_create(arr, len(self.plans), _stream_ptr(stream), ctypes.byref(h)), None)
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib.nufft_frames_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def selfadjoint_multicoil(self, coils, x, out=None):
+        """out[f] = sum_i conj(c_i) A_f^H A_f (c_i x[f]); x, out: (nframes, *Nd)."""
+        nf = len(self.plans)
+        n = 1
+        for v in self.Nd:
+            n *= v
+        if coils.dim() != len(self.Nd) + 1 or tuple(coils.shape[1:]) != self.Nd:
+            raise ValueError("coils must have shape (nc, *Nd)")
+        nc = int(coils.shape[0])
+        out = torch.empty((nf,) + self.Nd, dtype=torch.complex64, device=self.device) if out is None else out
+        check(lib.nufft_frames_set_stream(self._h, _stream_ptr()), None)
+        check(lib.nufft_frames_selfadjoint_multicoil(self._h, _dev_ptr(coils, nc * n, "coils"), nc,
+                                                     _dev_ptr(x, nf * n, "x"), _dev_ptr(out, nf * n, "out")), None)
+        return out
+
+
 # ---------------------------------------------------------------- same names as the C ABI
 def nufft_plan(om, Nd, Kd, Jd, stream=None) -> NufftPlan:
     return NufftPlan(om, Nd, Kd, Jd, stream)

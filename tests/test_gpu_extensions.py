@@ -234,3 +234,47 @@ def test_toeplitz_errors(nf):
     with nf.NufftPlan(dev(om), (512, 16), (1024, 32), (6, 6)) as plan:
         with pytest.raises(nf.NufftError):
             plan.toeplitz_init()                 # period P = 1024, grid 2P = 2048 exceeds the FFT sizes
+
+
+def test_frame_set_multicoil_normal_operator(nf):
+    """A frame set records every frame's multi-coil normal operator (Eq. 33 per
+    frame, uneven point counts) as one graph with concurrent branches: eager,
+    recording and replayed calls match the per-frame calls and the oracle."""
+    Nd, Kd, Jd = (32, 32), (64, 64), (6, 6)
+    frames = W.dynamic_radial_frames(4, 64)
+    nc = 3
+    coils = W.coil_maps(nc, Nd)
+    xs = cn((len(frames),) + Nd, 81)
+    plans = [nf.NufftPlan(dev(om), Nd, Kd, Jd) for om in frames]
+    try:
+        ref = [X.selfadjoint_multicoil(oracle.make_plan(om, Nd, Kd, Jd), coils.astype(np.complex128), xs[f])
+               for f, om in enumerate(frames)]
+        cd, xd = dev(coils), dev(xs)
+        single = [host(p.selfadjoint_multicoil(cd, xd[f])) for f, p in enumerate(plans)]
+        with nf.NufftFrames(plans) as fs:
+            out = torch.empty_like(xd)
+            for _ in range(4):                   # eager, record, replay, replay
+                out.zero_()
+                fs.selfadjoint_multicoil(cd, xd, out)
+                got = host(out)
+                for f in range(len(frames)):
+                    assert rel(got[f], single[f]) < 1e-5
+                    assert rel(got[f], ref[f]) < TOL_OP
+            with pytest.raises(nf.NufftError):
+                fs.selfadjoint_multicoil(cd, xd, xd)     # aliasing rejected
+    finally:
+        for p in plans:
+            p.close()
+
+
+def test_frame_set_rejects_mismatched_plans(nf):
+    a = nf.NufftPlan(dev(W.uniform_random_om(200, 2, seed=82)), (16, 16), (32, 32), (6, 6))
+    b = nf.NufftPlan(dev(W.uniform_random_om(200, 2, seed=83)), (32, 32), (64, 64), (6, 6))
+    try:
+        with pytest.raises(nf.NufftError):
+            nf.NufftFrames([a, b])
+        with pytest.raises(nf.NufftError):
+            nf.NufftFrames([a, a])
+    finally:
+        a.close()
+        b.close()
