@@ -129,16 +129,18 @@ extern "C" int nufft_trajectory_gradient(nufft_plan_t* p, const float* x_dev, co
   if (!x_dev || (p->M > 0 && (!g_dev || !gom_dev)))
     return set_error(p, NUFFT_EINVAL, "x_dev, g_dev or gom_dev is NULL");
   if (p->M == 0) return NUFFT_OK;
-  int rc = ensure_coef_derivatives(p);
-  if (rc != NUFFT_OK) return rc;
-  rc = launch_fft_forward(p, reinterpret_cast<const float2*>(x_dev), p->grid);
+  int rc = ensure_coef_derivatives(p);   // lazily, before any recording
   if (rc != NUFFT_OK) return rc;
   const float2* gy = reinterpret_cast<const float2*>(g_dev);
-  cudaError_t e;
-  switch (p->g.d) {
-    case 1: e = traj_grad_d<1>(p, p->grid, gy, gom_dev); break;
-    case 2: e = traj_grad_d<2>(p, p->grid, gy, gom_dev); break;
-    default: e = traj_grad_d<3>(p, p->grid, gy, gom_dev); break;
-  }
-  return e == cudaSuccess ? NUFFT_OK : cuda_check(p, e, "trajectory gradient kernel");
+  return run_graphed(p, 23, x_dev, gom_dev, graph_key({graph_bits(g_dev)}), [&]() -> int {
+    int r = launch_fft_forward(p, reinterpret_cast<const float2*>(x_dev), p->grid);
+    if (r != NUFFT_OK) return r;
+    cudaError_t e;
+    switch (p->g.d) {
+      case 1: e = traj_grad_d<1>(p, p->grid, gy, gom_dev); break;
+      case 2: e = traj_grad_d<2>(p, p->grid, gy, gom_dev); break;
+      default: e = traj_grad_d<3>(p, p->grid, gy, gom_dev); break;
+    }
+    return e == cudaSuccess ? NUFFT_OK : cuda_check(p, e, "trajectory gradient kernel");
+  });
 }

@@ -39,6 +39,11 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
 
 
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
 @pytest.mark.parametrize("Nd,Kd,Jd,gen", [
     ((40,), (128,), (6,), lambda: W.uniform_random_om(500, 1, seed=31)),
     ((32, 48), (64, 128), (6, 6), lambda: W.uniform_random_om(1500, 2, seed=32)),
@@ -54,7 +59,16 @@ def test_trajectory_gradient_matches_oracle(nf, Nd, Kd, Jd, gen):
         gom = plan.trajectory_gradient(dev(x), dev(g))
         torch.cuda.synchronize()
         gom = gom.cpu().numpy()
-    assert rel(gom, X.trajectory_gradient(ref, x, g)) < TOL_GRAD
+        assert rel(gom, X.trajectory_gradient(ref, x, g)) < TOL_GRAD
+        # eager, recording and replayed calls on the same buffers, new contents each time
+        xd, gd = dev(x), dev(g)
+        out = torch.empty((om.shape[0], len(Nd)), dtype=torch.float32, device=DEV)
+        for it in range(3):
+            x2, g2 = cn(Nd, 10 + it), cn(om.shape[0], 20 + it)
+            xd.copy_(torch.from_numpy(x2))
+            gd.copy_(torch.from_numpy(g2))
+            plan.trajectory_gradient(xd, gd, out)
+            assert rel(host(out), X.trajectory_gradient(ref, x2, g2)) < TOL_GRAD
 
 
 def test_autograd_quadratic_loss_matches_oracle(nf):
