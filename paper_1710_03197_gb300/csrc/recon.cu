@@ -48,12 +48,6 @@ __global__ void k_weight(const float2* y, const float* w, float2* out, int64_t n
     out[i] = cscale(y[i], w[i]);
 }
 
-// out = c . x
-__global__ void k_coil_mul(const float2* c, const float2* x, float2* out, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = cmul(c[i], x[i]);
-}
-
 // out[b] = c[b] . x for all nc coils (nc x n outputs)
 __global__ void k_coil_mul_all(const float2* c, const float2* x, float2* out, int64_t n, int nc) {
   const int64_t tot = n * nc;
@@ -103,7 +97,7 @@ int selfadjoint_multicoil_impl(nufft_plan_t* p, const float2* coils, int nc, con
   const int64_t n = p->Nprod;
   float2 *imgs, *res;      // coil images in, A^H A of each coil image out
   if (nc == 1) {
-    float2 *m0, *m1, *i0, *i1;
+    float2 *m0 = nullptr, *m1 = nullptr, *i0 = nullptr, *i1 = nullptr;
     TRY(get_aux(p, &m0, &m1, &i0, &i1));
     imgs = i0;
     res = i1;
@@ -122,7 +116,7 @@ int selfadjoint_multicoil_impl(nufft_plan_t* p, const float2* coils, int nc, con
 int adjoint_multicoil_impl(nufft_plan_t* p, const float2* coils, int nc, const float2* y, float2* x) {
   float2* imgs;
   if (nc == 1) {
-    float2 *m0, *m1, *i0, *i1;
+    float2 *m0 = nullptr, *m1 = nullptr, *i0 = nullptr, *i1 = nullptr;
     TRY(get_aux(p, &m0, &m1, &i0, &i1));
     imgs = i0;
   } else {
@@ -152,7 +146,7 @@ extern "C" int nufft_density_compensation(nufft_plan_t* p, float* w_dev, int ite
   TRY(check_plan_ptrs(p, {{w_dev, p ? p->M : 0}}));
   if (iters < 0) return set_error(p, NUFFT_EINVAL, "iters < 0");
   if (p->M == 0) return NUFFT_OK;
-  float2 *m0, *m1, *i0, *i1;
+  float2 *m0 = nullptr, *m1 = nullptr, *i0 = nullptr, *i1 = nullptr;
   TRY(get_aux(p, &m0, &m1, &i0, &i1));
   return run_graphed(p, 19, w_dev, nullptr, iters, [&]() -> int {
     for (int it = 0; it < iters; ++it) {
@@ -169,7 +163,7 @@ extern "C" int nufft_density_compensation(nufft_plan_t* p, float* w_dev, int ite
 
 extern "C" int nufft_gridding_recon(nufft_plan_t* p, const float* y_dev, const float* w_dev, float* x_dev) {
   TRY(check_plan_ptrs(p, {{y_dev, p ? p->M : 0}, {w_dev, p ? p->M : 0}, {x_dev, p ? p->Nprod : 0}}));
-  float2 *m0, *m1, *i0, *i1;
+  float2 *m0 = nullptr, *m1 = nullptr, *i0 = nullptr, *i1 = nullptr;
   TRY(get_aux(p, &m0, &m1, &i0, &i1));
   return run_graphed(p, 20, y_dev, x_dev, graph_key({graph_bits(w_dev)}), [&]() -> int {
     if (p->M > 0) {
@@ -186,7 +180,7 @@ extern "C" int nufft_forward_multicoil(nufft_plan_t* p, const float* coils_dev, 
   if (nc < 1) return set_error(p, NUFFT_EINVAL, "nc < 1");
   float2* imgs;
   if (nc == 1) {
-    float2 *m0, *m1, *i0, *i1;
+    float2 *m0 = nullptr, *m1 = nullptr, *i0 = nullptr, *i1 = nullptr;
     TRY(get_aux(p, &m0, &m1, &i0, &i1));
     imgs = i0;
   } else {
