@@ -19,8 +19,10 @@
  *   with image axis i.  Sample m measures
  *       y_m ~= sum_n x[n] exp(-i sum_i om[m,i] (n_i - N_i/2)).
  * - Pointers named *_dev are CUDA device pointers; *_host are host pointers.
- *   The caller owns every buffer it passes; no call keeps a caller pointer
- *   after it returns.  The plan owns everything it allocates.
+ *   The caller owns every buffer it passes; no call uses a caller buffer
+ *   after its work completes (a recorded graph, below, refers to the buffers
+ *   of the call that recorded it and runs again only for a call with the same
+ *   buffers).  The plan owns everything it allocates.
  * - Calls on device buffers are asynchronous and ordered on the plan's
  *   stream (set at plan creation, changeable with nufft_set_stream).  Input
  *   buffers must stay valid and unmodified until the work completes.
@@ -31,8 +33,9 @@
  * - CUDA graphs: nufft_forward, nufft_adjoint, nufft_selfadjoint, their
  *   host-buffer forms (copies included when both host buffers are
  *   page-locked; other host memory runs eagerly), the stage calls, the batch and
- *   multi-coil calls, density compensation, the gridding reconstruction and
- *   the solvers record their launch sequence into a CUDA graph on the second
+ *   multi-coil calls, density compensation, the gridding reconstruction, the
+ *   trajectory gradient and the solvers record their launch sequence into a
+ *   CUDA graph on the second
  *   call with the same buffers, parameters and stream, and replay it
  *   afterwards (one launch instead of up to a dozen per operator, and
  *   hundreds per solve).  The first call runs eagerly and does any lazy
