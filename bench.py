@@ -574,6 +574,7 @@ def run_differentiable(nf, torch, dev, reps: int = 5):
         torch.cuda.synchronize()
         res[key] = round((time.perf_counter() - t0) / reps * 1e3, 4)          # wall time, Python included
         res[key.replace("_ms", "_gpu_ms")] = round(e0.elapsed_time(e1) / reps, 4)   # stream time
+    res.update(_differentiable_graph(nf, torch, plan, om_d, x_d, y0, Nd, Kd, Jd, reps))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     plan.solve_l1tv_lad(y0, maxiter=50, inner=2, cg_iters=5, mu=1.0, lam=0.01)
@@ -584,6 +585,69 @@ def run_differentiable(nf, torch, dev, reps: int = 5):
     res["points"] = int(om.shape[0])
     plan.close()
     return res
+
+
+def _differentiable_graph(nf, torch, plan, om_d, x_d, y0, Nd, Kd, Jd, reps):
+    """The fixed-plan autograd step (forward, loss, backward to x and om)
+    captured once in a torch CUDA graph and replayed: the step's stream time
+    without the Python and ATen launch overhead of its ~20 small loss ops.
+    Beside it, the library calls of the step on their own: the forward as
+    its two stages, the adjoint and the trajectory gradient from the kept
+    spectrum."""
+    om_s = om_d.clone().requires_grad_(True)
+    x_s = x_d.clone().requires_grad_(True)
+
+    def step():
+        om_s.grad = None
+        x_s.grad = None
+        y = nf.nufft_apply(om_s, x_s, Nd, Kd, Jd, plan)
+        torch.sum(torch.abs(y - y0) ** 2).backward()
+
+    out = {}
+    try:
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(3):
+                step()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        for _ in range(2):
+            graph.replay()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            graph.replay()
+        e1.record()
+        e1.synchronize()
+        out["autograd_fixed_plan_graph_gpu_ms"] = round(e0.elapsed_time(e1) / reps, 4)
+        del graph
+    except RuntimeError as exc:   # capture refused by the runtime: report, do not fail the bench
+        out["autograd_fixed_plan_graph_gpu_ms"] = None
+        out["autograd_graph_error"] = str(exc).splitlines()[0][:200]
+    grid = plan.scale_pad_fft(x_d)
+    y = plan.interp(grid)
+    g = (y - y0).contiguous()
+    gx = plan.adjoint(g)
+    gom = plan.trajectory_gradient_grid(grid, g)
+    calls = (("scale_pad_fft_gpu_ms", lambda: plan.scale_pad_fft(x_d, grid)),
+             ("interp_gpu_ms", lambda: plan.interp(grid, y)),
+             ("adjoint_gpu_ms", lambda: plan.adjoint(g, gx)),
+             ("trajectory_gradient_grid_gpu_ms", lambda: plan.trajectory_gradient_grid(grid, g, gom)))
+    for key, fn in calls:
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps * 4):
+            fn()
+        e1.record()
+        e1.synchronize()
+        out[key] = round(e0.elapsed_time(e1) / (reps * 4), 4)
+    return out
 
 
 # ------------------------------------------------------------------ oracle timing (CPU baseline / reference arm)

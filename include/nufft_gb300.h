@@ -375,6 +375,18 @@ int nufft_set_normal_operator(nufft_plan_t* plan, int mode);
  */
 int nufft_trajectory_gradient(nufft_plan_t* plan, const float* x_dev, const float* g_dev, float* gom_dev);
 
+/*
+ * nufft_trajectory_gradient_grid - the same gradient from the oversampled
+ * spectrum Y = F S x instead of the image (Section 2.1, Eq. 1: the grid the
+ * interpolation reads), e.g. the grid nufft_scale_pad_fft wrote for the
+ * forward pass, so that a backward pass needs no second FFT.
+ *   grid_dev K^d complex64 in the plan's grid layout (as nufft_scale_pad_fft writes it)
+ *   g_dev, gom_dev as for nufft_trajectory_gradient
+ * Bit-identical to nufft_trajectory_gradient(x) when grid_dev holds
+ * nufft_scale_pad_fft(x).
+ */
+int nufft_trajectory_gradient_grid(nufft_plan_t* plan, const float* grid_dev, const float* g_dev, float* gom_dev);
+
 #ifdef __cplusplus
 }
 #endif

@@ -40,6 +40,7 @@ from .plan import (
     nufft_selfadjoint_multicoil,
     solve_cg_multicoil,
     nufft_trajectory_gradient,
+    nufft_trajectory_gradient_grid,
     nufft_forward_batch,
     nufft_adjoint_batch,
     nufft_selfadjoint_batch,
@@ -56,7 +57,7 @@ __all__ = [
     "nufft_gridding", "nufft_gridding_static", "nufft_ifft_crop_rescale", "solve_cg", "solve_l1tv_ols", "solve_l1tv_lad",
     "nufft_density_compensation", "nufft_gridding_recon", "solve_cg_kspace", "nufft_forward_multicoil",
     "nufft_adjoint_multicoil", "nufft_selfadjoint_multicoil", "solve_cg_multicoil",
-    "nufft_trajectory_gradient", "NufftFunction", "nufft_apply",
+    "nufft_trajectory_gradient", "nufft_trajectory_gradient_grid", "NufftFunction", "nufft_apply",
     "nufft_forward_batch", "nufft_adjoint_batch", "nufft_selfadjoint_batch",
     "nufft_toeplitz_init", "nufft_selfadjoint_toeplitz", "nufft_set_normal_operator",
 ]

@@ -68,6 +68,7 @@ _SIGS = {
     "nufft_frames_set_stream": (_i, [_vp, _vp]),
     "nufft_frames_selfadjoint_multicoil": (_i, [_vp, _vp, _i, _vp, _vp]),
     "nufft_trajectory_gradient": (_i, [_PLAN, _vp, _vp, _vp]),
+    "nufft_trajectory_gradient_grid": (_i, [_PLAN, _vp, _vp, _vp]),
     "nufft_forward_batch": (_i, [_PLAN, _i, _vp, _vp]),
     "nufft_adjoint_batch": (_i, [_PLAN, _i, _vp, _vp]),
     "nufft_selfadjoint_batch": (_i, [_PLAN, _i, _vp, _vp]),

@@ -2,8 +2,11 @@
 
 Backward (both by the library's kernels):
 * image gradient: A^H g (nufft_adjoint), since y is linear in x;
-* trajectory gradient: Re(conj(g) dy/dom) (nufft_trajectory_gradient), through
-  the min-max coefficients' derivative with the neighbourhood held fixed.
+* trajectory gradient: Re(conj(g) dy/dom) (nufft_trajectory_gradient_grid),
+  through the min-max coefficients' derivative with the neighbourhood held
+  fixed.  When om needs a gradient the forward runs as its two stages
+  (nufft_scale_pad_fft, nufft_interp) and keeps the oversampled spectrum F S x
+  for the backward pass, which then needs no FFT of its own.
 A plan is built for the given trajectory on every forward call (the
 interpolator depends on om); pass ``plan`` to reuse one for a fixed om.
 """
@@ -20,18 +23,24 @@ class NufftFunction(torch.autograd.Function):
         om_c = om.detach().to(torch.float32).contiguous()
         x_c = x.detach().to(torch.complex64).contiguous()
         p = plan if plan is not None else NufftPlan(om_c, Nd, Kd, Jd)
-        y = p.forward(x_c)
+        if ctx.needs_input_grad[0]:
+            grid = p.scale_pad_fft(x_c)
+            y = p.interp(grid)
+            ctx.save_for_backward(grid)
+        else:
+            y = p.forward(x_c)
         ctx.plan = p
-        ctx.save_for_backward(x_c)
         return y
 
     @staticmethod
     def backward(ctx, gy):
-        (x_c,) = ctx.saved_tensors
         p = ctx.plan
         gy = gy.to(torch.complex64).contiguous()
         gx = p.adjoint(gy) if ctx.needs_input_grad[1] else None
-        gom = p.trajectory_gradient(x_c, gy) if ctx.needs_input_grad[0] else None
+        gom = None
+        if ctx.needs_input_grad[0]:
+            (grid,) = ctx.saved_tensors
+            gom = p.trajectory_gradient_grid(grid, gy)
         return gom, gx, None, None, None, None
 
 

@@ -144,3 +144,24 @@ extern "C" int nufft_trajectory_gradient(nufft_plan_t* p, const float* x_dev, co
     return e == cudaSuccess ? NUFFT_OK : cuda_check(p, e, "trajectory gradient kernel");
   });
 }
+
+extern "C" int nufft_trajectory_gradient_grid(nufft_plan_t* p, const float* grid_dev, const float* g_dev,
+                                              float* gom_dev) {
+  if (!p) return set_error(nullptr, NUFFT_EINVAL, "plan is NULL");
+  if (!grid_dev || (p->M > 0 && (!g_dev || !gom_dev)))
+    return set_error(p, NUFFT_EINVAL, "grid_dev, g_dev or gom_dev is NULL");
+  if (p->M == 0) return NUFFT_OK;
+  int rc = ensure_coef_derivatives(p);
+  if (rc != NUFFT_OK) return rc;
+  const float2* grid = reinterpret_cast<const float2*>(grid_dev);
+  const float2* gy = reinterpret_cast<const float2*>(g_dev);
+  return run_graphed(p, 24, grid_dev, gom_dev, graph_key({graph_bits(g_dev)}), [&]() -> int {
+    cudaError_t e;
+    switch (p->g.d) {
+      case 1: e = traj_grad_d<1>(p, grid, gy, gom_dev); break;
+      case 2: e = traj_grad_d<2>(p, grid, gy, gom_dev); break;
+      default: e = traj_grad_d<3>(p, grid, gy, gom_dev); break;
+    }
+    return e == cudaSuccess ? NUFFT_OK : cuda_check(p, e, "trajectory gradient kernel");
+  });
+}

@@ -287,6 +287,14 @@ class NufftPlan:
                                             _dev_ptr(gom, self.M * self.d, "gom", dtype=torch.float32)), self._h)
         return gom
 
+    def trajectory_gradient_grid(self, grid, g, gom=None):
+        """The same gradient from the oversampled spectrum F S x (C: nufft_trajectory_gradient_grid)."""
+        gom = torch.empty((self.M, self.d), dtype=torch.float32, device=self.device) if gom is None else gom
+        self._sync_stream()
+        check(lib.nufft_trajectory_gradient_grid(self._h, _dev_ptr(grid, self.Kprod, "grid"), _dev_ptr(g, self.M, "g"),
+                                                 _dev_ptr(gom, self.M * self.d, "gom", dtype=torch.float32)), self._h)
+        return gom
+
     # ---------------------------------------------------------------- density compensation, k-space CG
     def density_compensation(self, iters: int, w=None):
         """Pipe-Menon weights (Eq. 5); w: float32 CUDA tensor of M starting weights (default ones)."""
@@ -490,6 +498,10 @@ def solve_cg_multicoil(plan: NufftPlan, coils, y, x=None, maxiter=20):
 
 def nufft_trajectory_gradient(plan: NufftPlan, x, g, gom=None):
     return plan.trajectory_gradient(x, g, gom)
+
+
+def nufft_trajectory_gradient_grid(plan: NufftPlan, grid, g, gom=None):
+    return plan.trajectory_gradient_grid(grid, g, gom)
 
 
 def nufft_forward_batch(plan: NufftPlan, x, y=None):

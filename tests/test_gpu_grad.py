@@ -69,6 +69,15 @@ def test_trajectory_gradient_matches_oracle(nf, Nd, Kd, Jd, gen):
             gd.copy_(torch.from_numpy(g2))
             plan.trajectory_gradient(xd, gd, out)
             assert rel(host(out), X.trajectory_gradient(ref, x2, g2)) < TOL_GRAD
+        # from the oversampled spectrum: the same kernel on the same grid, so bit-identical
+        grid = plan.scale_pad_fft(xd)
+        out_g = torch.empty_like(out)
+        for it in range(3):
+            g3 = cn(om.shape[0], 30 + it)
+            gd.copy_(torch.from_numpy(g3))
+            plan.trajectory_gradient_grid(grid, gd, out_g)
+            plan.trajectory_gradient(xd, gd, out)
+            assert np.array_equal(host(out_g), host(out))
 
 
 def test_autograd_quadratic_loss_matches_oracle(nf):
@@ -91,6 +100,30 @@ def test_autograd_quadratic_loss_matches_oracle(nf):
     assert rel(om_t.grad.cpu().numpy(), X.trajectory_gradient(ref, x, g)) < TOL_GRAD
 
 
+@pytest.mark.parametrize("which", ["x", "om"])
+def test_autograd_one_input_needs_grad(nf, which):
+    """Only one of x, om requires a gradient: the forward then runs as one call
+    (x) or as its two stages with the spectrum kept (om)."""
+    Nd, Kd, Jd = (24, 40), (64, 128), (6, 6)
+    om = W.uniform_random_om(900, 2, seed=41)
+    x = cn(Nd, 5)
+    y0 = cn(om.shape[0], 6)
+    om_t = dev(om).requires_grad_(which == "om")
+    x_t = dev(x).requires_grad_(which == "x")
+    y = nf.nufft_apply(om_t, x_t, Nd, Kd, Jd)
+    y.retain_grad()
+    torch.sum(torch.abs(y - dev(y0)) ** 2).backward()
+    ref = oracle.make_plan(om, Nd, Kd, Jd)
+    assert rel(host(y.detach()), oracle.forward(ref, x)) < TOL_OP
+    g = y.grad.cpu().numpy().astype(np.complex128)
+    if which == "x":
+        assert om_t.grad is None
+        assert rel(x_t.grad.cpu().numpy(), oracle.adjoint(ref, g)) < TOL_OP
+    else:
+        assert x_t.grad is None
+        assert rel(om_t.grad.cpu().numpy(), X.trajectory_gradient(ref, x, g)) < TOL_GRAD
+
+
 def test_spiral2d_256_gradients_full_size(nf):
     """The 256^2 spiral workload (16 x 2048 points, om perturbed by N(0, 1e-3))."""
     spec, om, x, noise = W.make_workload("spiral2d_256")
@@ -107,3 +140,50 @@ def test_spiral2d_256_gradients_full_size(nf):
     g = y.grad.cpu().numpy().astype(np.complex128)
     assert rel(x_t.grad.cpu().numpy(), oracle.adjoint(ref, g)) < TOL_OP
     assert rel(om_t.grad.cpu().numpy(), X.trajectory_gradient(ref, x, g)) < TOL_GRAD
+
+
+def test_autograd_step_in_a_torch_cuda_graph(nf):
+    """Forward, loss and backward captured in one torch CUDA graph (the library
+    calls launch into the caller's capture) and replayed with new image
+    contents: gradients match the oracle's on every replay."""
+    Nd, Kd, Jd = (32, 32), (64, 64), (6, 6)
+    om = W.spiral2d(6, 400)
+    y0 = cn(om.shape[0], 7)
+    ref = oracle.make_plan(om, Nd, Kd, Jd)
+    plan = nf.NufftPlan(dev(om), Nd, Kd, Jd)
+    om_s = dev(om).requires_grad_(True)
+    x_s = dev(cn(Nd, 8)).requires_grad_(True)
+    y0d = dev(y0)
+    holder = {}
+
+    def step():
+        om_s.grad = None
+        x_s.grad = None
+        y = nf.nufft_apply(om_s, x_s, Nd, Kd, Jd, plan)
+        y.retain_grad()
+        torch.sum(torch.abs(y - y0d) ** 2).backward()
+        holder["y"] = y
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            step()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    for it in range(3):
+        x = cn(Nd, 50 + it)
+        with torch.no_grad():
+            x_s.copy_(torch.from_numpy(x))
+        graph.replay()
+        torch.cuda.synchronize()
+        r = oracle.forward(ref, x) - y0
+        g = holder["y"].grad.cpu().numpy().astype(np.complex128)
+        assert rel(g, 2 * r) < 1e-4
+        assert rel(x_s.grad.cpu().numpy(), oracle.adjoint(ref, g)) < TOL_OP
+        assert rel(om_s.grad.cpu().numpy(), X.trajectory_gradient(ref, x, g)) < TOL_GRAD
+    del graph
+    plan.close()
