@@ -39,8 +39,12 @@ namespace nufft {
 // A^H A x, used by the solvers too.
 int selfadjoint_impl(nufft_plan_t* p, const float2* x, float2* out) {
   TRY(launch_fft_forward(p, x, p->grid));
-  TRY(launch_interp(p, p->grid, p->ytmp));
-  TRY(launch_gridding(p, p->ytmp, p->grid));
+  if (vhv_fused(p)) {
+    TRY(launch_vhv(p, p->grid, p->grid));     // gather then scatter per tile chunk
+  } else {
+    TRY(launch_interp(p, p->grid, p->ytmp));
+    TRY(launch_gridding(p, p->ytmp, p->grid));
+  }
   return launch_fft_inverse(p, p->grid, out);
 }
 int forward_dev(nufft_plan_t* p, const float2* x, float2* y) { return forward_impl(p, x, y); }
@@ -86,8 +90,12 @@ int selfadjoint_batch_impl(nufft_plan_t* p, int nb, const float2* x, float2* out
   if (nb == 1) return selfadjoint_impl(p, x, out);
   TRY(ensure_batch(p, nb));
   TRY(launch_fft_forward(p, x, p->bgrid, nb));
-  TRY(launch_interp(p, p->bgrid, p->bytmp, nb));
-  TRY(launch_gridding(p, p->bytmp, p->bgrid, nb, p->btiles));
+  if (vhv_fused(p)) {
+    TRY(launch_vhv(p, p->bgrid, p->bgrid, nb, p->btiles));
+  } else {
+    TRY(launch_interp(p, p->bgrid, p->bytmp, nb));
+    TRY(launch_gridding(p, p->bytmp, p->bgrid, nb, p->btiles));
+  }
   return launch_fft_inverse(p, p->bgrid, out, nb);
 }
 }  // namespace nufft

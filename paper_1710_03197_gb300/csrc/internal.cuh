@@ -163,6 +163,10 @@ int launch_fft_inverse(nufft_plan_t* p, float2* grid, float2* x, int nb = 1, boo
 // (nb x nchunks x padded tile; NULL = the plan's single-batch buffer).
 int launch_interp(nufft_plan_t* p, const float2* grid, float2* y, int nb = 1);
 int launch_gridding(nufft_plan_t* p, const float2* y, float2* grid, int nb = 1, float2* tiles = nullptr);
+// V^H V on the oversampled grid in one chunk pass (2D): grid_in -> grid_out
+// (they may be the same buffer); vhv_fused tells whether the plan has it.
+bool vhv_fused(const nufft_plan_t* p);
+int launch_vhv(nufft_plan_t* p, const float2* grid_in, float2* grid_out, int nb = 1, float2* tiles = nullptr);
 
 // Batched operators (capi.cu): nb transforms with one launch per stage.
 int ensure_batch(nufft_plan_t* p, int nb);

@@ -396,7 +396,12 @@ k_gridding_reduce(const float2* __restrict__ tiles_b, const int32_t* __restrict_
 // point read consecutive words, so a warp's 64-bit reads of five points hit
 // distinct bank pairs), y[cap], k[2][cap] (first neighbours relative to the
 // tile origin), cap = chunk size.
-template <int JF>
+// FUSED (V^H V, the normal operator's grid part): y_b is the oversampled
+// spectrum instead of the samples, and each point's y is gathered from it in
+// the scatter's own lane layout (the interpolation's arithmetic and summation
+// order) right before it is scattered, so the samples never leave the CTA and
+// the coefficients are read once for both directions.
+template <int JF, bool FUSED>
 __global__ void __launch_bounds__(256, 4)
 k_gridding_chunk_staged(const float2* __restrict__ y_b, float2* __restrict__ tiles_b,
                         const Chunk* __restrict__ chunks, const Points P, const Geom g, int64_t ybs, int64_t tbs) {
@@ -423,7 +428,7 @@ k_gridding_chunk_staged(const float2* __restrict__ y_b, float2* __restrict__ til
   if (qs < ch.count) {
     const int q = qs;
     const int64_t i = (int64_t)ch.start + q;
-    pm = P.perm[i];
+    if (!FUSED) pm = P.perm[i];
     s_k[q] = P.kf[i] - org0;
     s_k[cap + q] = P.kf[P.M + i] - org1;
 #pragma unroll
@@ -437,7 +442,7 @@ k_gridding_chunk_staged(const float2* __restrict__ y_b, float2* __restrict__ til
       s_c[J0 * cap + q * J1 + r] = P.coef[P.coef_off[1] + (int64_t)r * P.M + i];
     }
   }
-  if (qs < ch.count) s_y[qs] = __ldg(&y[pm]);
+  if (!FUSED && qs < ch.count) s_y[qs] = __ldg(&y[pm]);
   __syncthreads();
 
   const int G = J1;
@@ -448,7 +453,50 @@ k_gridding_chunk_staged(const float2* __restrict__ y_b, float2* __restrict__ til
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
   const int P1 = g.P[1];
-  if (sub < per_warp) {
+  if (FUSED) {
+    // warp-uniform rounds of per_warp points: the lane-group sum is a
+    // full-warp shuffle
+    const int K0m = g.K[0] - 1, K1m = g.K[1] - 1;
+    const int ks0 = (int)g.Kstride[0];
+    for (int qb = warp * per_warp; qb < ch.count; qb += nwarps * per_warp) {
+      const int q = qb + sub;
+      const bool act = (sub < per_warp) && (q < ch.count);
+      float2 part = make_float2(0.f, 0.f);
+      float2 cl = make_float2(0.f, 0.f);
+      if (act) {
+        const int gl = (s_k[cap + q] + org1 + l) & K1m;
+        const int k0 = s_k[q] + org0;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j0 = 0; j0 < (JF > 0 ? JF : kMaxJ); ++j0) {
+          if (JF == 0 && j0 >= J0) break;
+          acc = cadd(acc, cmul(s_c[j0 * cap + q], __ldg(&y[((k0 + j0) & K0m) * ks0 + gl])));
+        }
+        cl = s_c[J0 * cap + q * J1 + l];
+        part = cmul(cl, acc);
+      }
+      const int base = sub * G;
+      float2 yv = make_float2(0.f, 0.f);
+      for (int r = 0; r < G; ++r) {
+        const int src = (base + r) & 31;
+        yv.x += __shfl_sync(0xffffffffu, part.x, src);
+        yv.y += __shfl_sync(0xffffffffu, part.y, src);
+      }
+      if (act) {
+        const float2 yl = cmulc(cl, yv);   // conj(c_last) * y
+        const int ll = s_k[cap + q] + l;
+        const int l0 = s_k[q];
+#pragma unroll
+        for (int j0 = 0; j0 < (JF > 0 ? JF : kMaxJ); ++j0) {
+          if (JF == 0 && j0 >= J0) break;
+          const float2 w = cmulc(s_c[j0 * cap + q], yl);
+          const int cell = (l0 + j0) * P1 + ll;
+          atomicAdd(&sre[cell], w.x);
+          atomicAdd(&sim[cell], w.y);
+        }
+      }
+    }
+  } else if (sub < per_warp) {
     for (int q = warp * per_warp + sub; q < ch.count; q += nwarps * per_warp) {
       const float2 yl = cmulc(s_c[J0 * cap + q * J1 + l], s_y[q]);   // conj(c_last) * y
       const int ll = s_k[cap + q] + l;
@@ -505,7 +553,8 @@ cudaError_t interp_d(const nufft_plan_t* p, const float2* grid, float2* y, int n
 }
 
 // Chunk pass of V^H: one CTA per (chunk, batch element), partial tiles out.
-template <int D>
+// FUSED (2D only): y is the oversampled spectrum and the pass computes V^H V.
+template <int D, bool FUSED = false>
 cudaError_t launch_chunks(const nufft_plan_t* p, const float2* y, float2* tiles, int nb, int64_t ybs, int64_t tbs) {
   if (p->nchunks == 0) return cudaSuccess;
   const Points P = points_view(p);
@@ -516,11 +565,12 @@ cudaError_t launch_chunks(const nufft_plan_t* p, const float2* y, float2* tiles,
     const int sj = p->g.J[0] + p->g.J[1];
     const size_t smem = (size_t)p->g.padded_cells * sizeof(float2) +
                         (size_t)kChunkPoints[2] * ((size_t)sj * sizeof(float2) + sizeof(float2) + 2 * sizeof(int));
-    auto kern = j6 ? k_gridding_chunk_staged<6> : k_gridding_chunk_staged<0>;
+    auto kern = j6 ? k_gridding_chunk_staged<6, FUSED> : k_gridding_chunk_staged<0, FUSED>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<gd, kChunkPoints[2], smem, p->stream>>>(y, tiles, p->chunks, P, p->g, ybs, tbs);
   } else {
+    static_assert(!FUSED, "the fused V^H V pass is 2D only");
     const size_t smem = (size_t)p->g.padded_cells * sizeof(float2);
     constexpr int NT = GridChunkCfg<D, 6>::kThreads;
     bool t16 = D == 3;
@@ -583,6 +633,17 @@ int launch_interp(nufft_plan_t* p, const float2* grid, float2* y, int nb) {
     default: e = interp_d<3>(p, grid, y, nb); break;
   }
   return e == cudaSuccess ? NUFFT_OK : cuda_check(p, e, "interpolation kernel");
+}
+
+bool vhv_fused(const nufft_plan_t* p) { return p->g.d == 2 && p->M > 0; }
+
+int launch_vhv(nufft_plan_t* p, const float2* grid_in, float2* grid_out, int nb, float2* tiles) {
+  if (!vhv_fused(p)) return set_error(p, NUFFT_EINVAL, "fused V^H V is 2D only");
+  if (!tiles) tiles = p->tiles;
+  const int64_t tbs = p->nchunks * p->g.padded_cells;
+  cudaError_t e = launch_chunks<2, true>(p, grid_in, tiles, nb, p->Kprod, tbs);
+  if (e == cudaSuccess) e = launch_reduce<2>(p, tiles, grid_out, nb);
+  return e == cudaSuccess ? NUFFT_OK : cuda_check(p, e, "fused V^H V kernels");
 }
 
 int launch_gridding(nufft_plan_t* p, const float2* y, float2* grid, int nb, float2* tiles) {

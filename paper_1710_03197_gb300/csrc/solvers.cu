@@ -462,6 +462,7 @@ extern "C" int solve_cg_kspace(nufft_plan_t* p, const float* y_dev, float* x_dev
     TRY(launch_gridding(p, reinterpret_cast<const float2*>(y_dev), b));          // V^H y
     NUFFT_CUDA_TRY(p, cudaMemsetAsync(k, 0, n * sizeof(float2), st));
     auto vhv = [&](const float2* in, float2* out) -> int {                       // V^H V
+      if (vhv_fused(p)) return launch_vhv(p, in, out);
       TRY(launch_interp(p, in, p->ytmp));
       return launch_gridding(p, p->ytmp, out);
     };
