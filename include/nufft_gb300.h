@@ -165,7 +165,8 @@ int nufft_selfadjoint(nufft_plan_t* plan, const float* x_dev, float* out_dev);
  * result is in host memory (the plan's stream is synchronized).  With
  * page-locked host buffers (cudaHostAlloc, cudaHostRegister) the FFT reads or
  * writes the image in host memory directly and only the k-space samples are
- * copied; any other host memory is copied through the plan's device staging
+ * copied (by a copy kernel through the buffer's device address, not a
+ * copy-engine transfer); any other host memory is copied through the plan's device staging
  * buffers.  The buffers must stay valid and, if page-locked, stay page-locked
  * until the call returns. */
 int nufft_forward_host(nufft_plan_t* plan, const float* x_host, float* y_host);

@@ -216,9 +216,12 @@ def test_selfadjoint_matches_oracle(case):
     ((24, 40), (64, 128), (6, 6), lambda: W.uniform_random_om(3001, 2, seed=22)),
     ((32, 32), (64, 64), (5, 7), lambda: W.uniform_random_om(2049, 2, seed=23)),
     ((16, 32), (16, 32), (1, 3), lambda: W.uniform_random_om(513, 2, seed=24)),
+    ((24, 32, 16), (64, 64, 32), (6, 6, 6), lambda: W.kooshball3d(300, 64)),
+    ((16, 16, 16), (32, 32, 32), (4, 5, 6), lambda: W.uniform_random_om(1500, 3, seed=25)),
 ])
 def test_fused_normal_operator_equals_forward_then_adjoint(nf, Nd, Kd, Jd, gen):
-    """2D A^H A runs V^H V as one gather-then-scatter pass per tile chunk; it
+    """2D A^H A runs V^H V as one gather-then-scatter pass per tile chunk (1D
+    and 3D run V then V^H); it
     must agree with the separate forward and adjoint calls (the same
     arithmetic up to the gridding's atomic summation order), singly and
     batched."""
