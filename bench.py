@@ -534,8 +534,9 @@ def run_multicoil_dynamic(nf, torch, dev, reps: int = 5):
 
 def run_differentiable(nf, torch, dev, reps: int = 5):
     """256^2 spiral (16 x 2048, om + N(0, 1e-3)): forward + backward through the
-    autograd function (plan rebuilt each step, since om is a variable) against
-    the plain forward + adjoint with a fixed plan; then 50 L1TV-LAD iterations."""
+    autograd function with a plan rebuilt each step, with one plan moved to
+    each step's trajectory (nufft_plan_set_trajectory) and with a fixed plan,
+    against the plain forward + adjoint; then 50 L1TV-LAD iterations."""
     spec, om, x, noise = W.make_workload("spiral2d_256")
     Nd, Kd, Jd = spec["Nd"], spec["Kd"], spec["Jd"]
     om_d = torch.from_numpy(om).to(dev)
@@ -559,9 +560,28 @@ def run_differentiable(nf, torch, dev, reps: int = 5):
         y = plan.forward(x_d)
         plan.adjoint((y - y0).contiguous())
 
+    # a trajectory that moves every step (an optimisation loop over om): one
+    # plan moved by nufft_plan_set_trajectory instead of a new plan per step
+    g = torch.Generator(device=dev).manual_seed(5)
+    moved = [(om_d + 1e-4 * torch.randn(om_d.shape, device=dev, generator=g)).contiguous() for _ in range(4)]
+    plan_r = nf.NufftPlan(om_d, Nd, Kd, Jd)
+    it = [0]
+
+    def diff_step_moving_plan():
+        om_t = moved[it[0] % len(moved)].clone().requires_grad_(True)
+        it[0] += 1
+        x_t = x_d.clone().requires_grad_(True)
+        y = nf.nufft_apply(om_t, x_t, Nd, Kd, Jd, plan_r, refresh=True)
+        torch.sum(torch.abs(y - y0) ** 2).backward()
+
+    def set_trajectory_only():
+        plan_r.set_trajectory(moved[it[0] % len(moved)])
+        it[0] += 1
+
     res = {}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for key, fn in (("autograd_with_plan_ms", diff_step), ("autograd_fixed_plan_ms", diff_step_fixed_plan),
+                    ("autograd_moving_plan_ms", diff_step_moving_plan), ("set_trajectory_ms", set_trajectory_only),
                     ("plain_fwd_adj_ms", plain_step)):
         fn()
         fn()
@@ -581,6 +601,7 @@ def run_differentiable(nf, torch, dev, reps: int = 5):
     e1.record()
     e1.synchronize()
     res["l1tv_lad_50_iterations_ms"] = round(e0.elapsed_time(e1), 3)
+    plan_r.close()
     res["workload"] = "256^2 ellipse phantom, 16 spiral interleaves x 2048 samples (32,768 points), grid 512^2, J=6x6"
     res["points"] = int(om.shape[0])
     plan.close()

@@ -117,6 +117,23 @@ int nufft_plan_destroy(nufft_plan_t* plan);
  * plan-less call on this host thread).  Never NULL; valid until the next call. */
 const char* nufft_last_error(const nufft_plan_t* plan);
 
+/*
+ * nufft_plan_set_trajectory - give the plan a new trajectory of the same M
+ * points (om_dev: M x d float32 row-major radians, as for nufft_plan; the
+ * caller keeps it).  Only what depends on the points is redone (Section
+ * 2.1.3's interpolator: the tile sort, the chunk list, the per-point
+ * coefficients, and their trajectory derivative if the plan has computed it);
+ * the scaling factors, the min-max inverses, their Chebyshev expansions and
+ * the work space are kept, the chunk list and partial tiles grow when the new
+ * points need more.  Recorded graphs are dropped (frame sets over the plan
+ * re-record), a Toeplitz kernel is discarded (the solvers' normal operator
+ * goes back to V^H V until nufft_toeplitz_init is called again).
+ * Synchronizes the stream.  Errors: NUFFT_EINVAL for a NULL argument or a
+ * non-finite / out-of-range om, with the plan unchanged; NUFFT_ECUDA /
+ * NUFFT_ENOMEM leave the plan unusable (destroy it).
+ */
+int nufft_plan_set_trajectory(nufft_plan_t* plan, const float* om_dev);
+
 /* Change the stream the plan's work is ordered on (cudaStream_t as void*). */
 int nufft_set_stream(nufft_plan_t* plan, void* stream);
 

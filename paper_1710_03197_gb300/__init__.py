@@ -19,6 +19,7 @@ from .plan import (
     NufftFrames,
     nufft_plan,
     nufft_plan_tuned,
+    nufft_plan_set_trajectory,
     nufft_forward,
     nufft_adjoint,
     nufft_selfadjoint,
@@ -52,7 +53,7 @@ from .autograd import NufftFunction, nufft_apply
 
 __all__ = [
     "lib", "LIB_PATH", "NufftError", "check", "symbols_declared", "NufftPlan", "NufftFrames",
-    "nufft_plan", "nufft_plan_tuned", "nufft_forward", "nufft_adjoint", "nufft_selfadjoint",
+    "nufft_plan", "nufft_plan_tuned", "nufft_plan_set_trajectory", "nufft_forward", "nufft_adjoint", "nufft_selfadjoint",
     "nufft_forward_host", "nufft_adjoint_host", "nufft_scale_pad_fft", "nufft_interp",
     "nufft_gridding", "nufft_gridding_static", "nufft_ifft_crop_rescale", "solve_cg", "solve_l1tv_ols", "solve_l1tv_lad",
     "nufft_density_compensation", "nufft_gridding_recon", "solve_cg_kspace", "nufft_forward_multicoil",

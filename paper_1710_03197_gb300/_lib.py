@@ -40,6 +40,7 @@ _SIGS = {
     "nufft_plan_destroy": (_i, [_PLAN]),
     "nufft_last_error": (ctypes.c_char_p, [_PLAN]),
     "nufft_set_stream": (_i, [_PLAN, _vp]),
+    "nufft_plan_set_trajectory": (_i, [_PLAN, _vp]),
     "nufft_set_graphs": (_i, [_PLAN, _i]),
     "nufft_plan_info": (_i, [_PLAN, ctypes.POINTER(_i64)]),
     "nufft_plan_get_interpolator": (_i, [_PLAN, _vp, _vp, _vp, _vp]),

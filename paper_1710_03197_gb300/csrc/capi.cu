@@ -60,7 +60,7 @@ int ensure_batch(nufft_plan_t* p, int nb) {
   for (float2** b : {&p->bgrid, &p->btiles, &p->bytmp, &p->bimg})
     if (*b) { cudaFree(*b); *b = nullptr; }
   p->batch_cap = 0;
-  const int64_t counts[4] = {(int64_t)nb * p->Kprod, (int64_t)nb * p->nchunks * p->g.padded_cells,
+  const int64_t counts[4] = {(int64_t)nb * p->Kprod, (int64_t)nb * p->chunk_cap * p->g.padded_cells,
                              (int64_t)nb * (p->M > 0 ? p->M : 1), (int64_t)nb * p->Nprod};
   float2** bufs[4] = {&p->bgrid, &p->btiles, &p->bytmp, &p->bimg};
   for (int k = 0; k < 4; ++k) {

@@ -31,6 +31,7 @@ struct nufft_frames {
   const void* kx = nullptr;
   const void* kout = nullptr;
   int knc = 0;
+  std::vector<uint64_t> kgen;           // the plans' generations when the key was taken
   int state = 0;
   cudaGraphExec_t exec = nullptr;
 };
@@ -130,8 +131,10 @@ extern "C" int nufft_frames_selfadjoint_multicoil(nufft_frames_t* fs, const floa
     cudaGetLastError();
     return run_frames(fs, coils, nc, x, out, false);   // inside the caller's capture
   }
-  const bool same = fs->kcoils == coils_dev && fs->kx == x_dev && fs->kout == out_dev && fs->knc == nc;
-  if (!same || fs->state == 0) {   // first use of these buffers: eager (lazy allocations happen here)
+  bool same = fs->kcoils == coils_dev && fs->kx == x_dev && fs->kout == out_dev && fs->knc == nc &&
+              fs->kgen.size() == fs->plans.size();
+  for (size_t f = 0; same && f < fs->plans.size(); ++f) same = fs->kgen[f] == fs->plans[f]->generation;
+  if (!same || fs->state == 0) {   // first use of these buffers (or a plan changed): eager
     if (fs->exec) cudaGraphExecDestroy(fs->exec);
     fs->exec = nullptr;
     fs->kcoils = coils_dev;
@@ -139,7 +142,10 @@ extern "C" int nufft_frames_selfadjoint_multicoil(nufft_frames_t* fs, const floa
     fs->kout = out_dev;
     fs->knc = nc;
     fs->state = 1;
-    return run_frames(fs, coils, nc, x, out, false);
+    const int rc = run_frames(fs, coils, nc, x, out, false);   // lazy allocations happen here
+    fs->kgen.resize(fs->plans.size());
+    for (size_t f = 0; f < fs->plans.size(); ++f) fs->kgen[f] = fs->plans[f]->generation;
+    return rc;
   }
   if (fs->state == 3) return run_frames(fs, coils, nc, x, out, false);
   if (fs->state == 1) {   // second use: record the frames as branches of one graph

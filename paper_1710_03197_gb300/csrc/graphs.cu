@@ -10,6 +10,7 @@
 namespace nufft {
 
 void drop_graphs(nufft_plan_t* p) {
+  ++p->generation;   // graphs recorded elsewhere (frame sets) over this plan are stale too
   for (int i = 0; i < kGraphSlots; ++i) {
     if (p->graphs[i].state == 2 && p->graphs[i].exec) cudaGraphExecDestroy(p->graphs[i].exec);
     p->graphs[i] = GraphEntry{};

@@ -116,6 +116,16 @@ struct nufft_plan {
   int cheb_ok[2];           // expansion used for the coefficients / their derivatives
   float2* dcoef;            // [sum_i J_i][M] d coef / d omega (allocated on first use)
 
+  // kept for nufft_plan_set_trajectory: sort scratch, the validation flags and
+  // the chunk capacity of chunks / tiles
+  uint32_t* sort_keys;      // [2][M]
+  int32_t* sort_vals;       // [M]
+  uint32_t* sort_hist;      // [256][ceil(M / sort tile)]
+  int32_t* perm2;           // [M]
+  int* flags;               // [2]: om invalid, G singular
+  int64_t chunk_cap;
+  uint64_t generation;      // bumped whenever recorded graphs may be stale (drop_graphs)
+
 
   // Toeplitz-embedded normal operator (nufft_toeplitz_init)
   nufft_plan* toep_geom;    // FFT geometry N in a 2N grid, no trajectory

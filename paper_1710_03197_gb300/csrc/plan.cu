@@ -548,84 +548,69 @@ void free_plan_memory(nufft_plan_t* p) {
   void* bufs[] = {p->s, p->twiddle, p->kf, p->coef, p->perm, p->bin_start, p->chunks, p->bin_chunk,
                   p->tiles, p->grid, p->ytmp, p->x_stage, p->y_stage, p->solver_ws, p->kspace_ws, p->mbuf,
                   p->s64, p->Tinv, p->om_sorted, p->dcoef, p->bgrid, p->btiles, p->bytmp, p->bimg,
-                  p->cheb};
+                  p->cheb, p->sort_keys, p->sort_vals, p->sort_hist, p->perm2, p->flags};
   for (void* b : bufs)
     if (b) cudaFree(b);
 }
 
-int build_plan(nufft_plan_t* p, const float* om) {
+DimTables dim_tables(const nufft_plan_t* p) {
+  DimTables D;
+  memset(&D, 0, sizeof(D));
+  D.d = p->g.d;
+  for (int a = 0; a < p->g.d; ++a) {
+    D.N[a] = p->g.N[a]; D.K[a] = p->g.K[a]; D.J[a] = p->g.J[a];
+    D.s_off[a] = p->s_off[a]; D.tw_off[a] = p->tw_off[a]; D.T_off[a] = p->T_off[a];
+  }
+  return D;
+}
+
+int sort_blocks(int64_t M) { return (int)((M + kSortItems - 1) / kSortItems); }
+
+// Reject a trajectory with a non-finite value or |om| > 2^20 (flag 0), before
+// anything uses it.  Synchronizes the stream.
+int validate_om(nufft_plan_t* p, const float* om) {
+  cudaStream_t st = p->stream;
+  NUFFT_CUDA_TRY(p, cudaMemsetAsync(p->flags, 0, sizeof(int), st));
+  if (p->M > 0) {
+    const int64_t n = p->M * p->g.d;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    k_validate<<<blocks, 256, 0, st>>>(om, n, p->flags);
+    NUFFT_CUDA_TRY(p, cudaGetLastError());
+  }
+  int bad = 0;
+  NUFFT_CUDA_TRY(p, cudaMemcpyAsync(&bad, p->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+  NUFFT_CUDA_TRY(p, cudaStreamSynchronize(st));
+  if (bad) return set_error(p, NUFFT_EINVAL, "om holds a non-finite value or |om| > 2^20");
+  return NUFFT_OK;
+}
+
+// Everything that depends on the trajectory (validated already): the tile
+// sort, the chunk list (chunks and partial tiles grown when it needs more),
+// the bank order, the per-point interpolator and, once the trajectory
+// gradient has been used, its derivative.  The per-dimension tables, the
+// Chebyshev expansions and every other buffer are the plan's already.
+int build_points(nufft_plan_t* p, const float* om) {
   Geom& g = p->g;
   const int d = g.d;
   const int64_t M = p->M;
   cudaStream_t st = p->stream;
-  int rc;
-
-  // ---- validate om on the device
-  int* flag = nullptr;
-  NUFFT_CUDA_TRY(p, cudaMalloc((void**)&flag, 2 * sizeof(int)));
-  struct FlagGuard { int* f; ~FlagGuard() { if (f) cudaFree(f); } } fg{flag};
-  NUFFT_CUDA_TRY(p, cudaMemsetAsync(flag, 0, 2 * sizeof(int), st));
-  if (M > 0) {
-    const int64_t n = M * d;
-    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
-    k_validate<<<blocks, 256, 0, st>>>(om, n, flag);
-    NUFFT_CUDA_TRY(p, cudaGetLastError());
-  }
-  int hflag[2] = {0, 0};
-  NUFFT_CUDA_TRY(p, cudaMemcpyAsync(hflag, flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-  NUFFT_CUDA_TRY(p, cudaStreamSynchronize(st));
-  if (hflag[0]) return set_error(p, NUFFT_EINVAL, "om holds a non-finite value or |om| > 2^20");
-
-  // ---- per-dimension tables
-  DimTables D;
-  memset(&D, 0, sizeof(D));
-  D.d = d;
-  int64_t s_tot = 0, tw_tot = 0, T_tot = 0;
-  for (int a = 0; a < d; ++a) {
-    D.N[a] = g.N[a]; D.K[a] = g.K[a]; D.J[a] = g.J[a];
-    D.s_off[a] = s_tot; D.tw_off[a] = tw_tot; D.T_off[a] = T_tot;
-    p->s_off[a] = s_tot; p->tw_off[a] = tw_tot;
-    s_tot += g.N[a]; tw_tot += g.K[a]; T_tot += (int64_t)g.J[a] * g.J[a];
-  }
-  NUFFT_CUDA_TRY(p, dalloc(p, &p->s, s_tot));
-  NUFFT_CUDA_TRY(p, dalloc(p, &p->twiddle, tw_tot));
-  NUFFT_CUDA_TRY(p, dalloc(p, &p->s64, s_tot));
-  NUFFT_CUDA_TRY(p, dalloc(p, &p->Tinv, T_tot));
-  for (int a = 0; a < d; ++a) p->T_off[a] = D.T_off[a];
-  double* s64 = p->s64;
-  double2* Tinv = p->Tinv;
-  struct Tmp { void* a; void* b; void* c; void* d; void* e; ~Tmp() { for (void* v : {a, b, c, d, e}) if (v) cudaFree(v); } } tmp{nullptr, nullptr, nullptr, nullptr, nullptr};
-  k_scaling_twiddle<<<d, 256, 0, st>>>(D, p->s, s64, p->twiddle);
-  NUFFT_CUDA_TRY(p, cudaGetLastError());
-  k_minmax_T<<<d, 256, 0, st>>>(D, s64, Tinv, flag + 1);
-  NUFFT_CUDA_TRY(p, cudaGetLastError());
 
   // ---- binning and stable sort by tile
-  NUFFT_CUDA_TRY(p, dalloc(p, &p->perm, M));
-  NUFFT_CUDA_TRY(p, dalloc(p, &p->bin_start, g.nbins + 1));
-  uint32_t *keyA = nullptr, *keyB = nullptr, *hist = nullptr;
-  int32_t* valB = nullptr;
   if (M > 0) {
-    NUFFT_CUDA_TRY(p, cudaMalloc((void**)&keyA, M * sizeof(uint32_t)));
-    tmp.c = keyA;
-    NUFFT_CUDA_TRY(p, cudaMalloc((void**)&keyB, M * sizeof(uint32_t)));
-    tmp.d = keyB;
-    NUFFT_CUDA_TRY(p, cudaMalloc((void**)&valB, M * sizeof(int32_t)));
-    tmp.e = valB;
+    uint32_t* keyA = p->sort_keys;
+    uint32_t* keyB = p->sort_keys + M;
     k_bins<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(om, M, g, keyA, p->perm);
     NUFFT_CUDA_TRY(p, cudaGetLastError());
-    const int nblk = (int)((M + kSortItems - 1) / kSortItems);
-    NUFFT_CUDA_TRY(p, cudaMalloc((void**)&hist, (size_t)256 * nblk * sizeof(uint32_t)));
-    struct HG { void* h; ~HG() { if (h) cudaFree(h); } } hg{hist};
+    const int nblk = sort_blocks(M);
     int bits = 0;
     while ((int64_t(1) << bits) < g.nbins) ++bits;
     const int passes = std::max(1, (bits + 7) / 8);
     uint32_t* kin = keyA; uint32_t* kout = keyB;
-    int32_t* vin = p->perm; int32_t* vout = valB;
+    int32_t* vin = p->perm; int32_t* vout = p->sort_vals;
     for (int pass = 0; pass < passes; ++pass) {
-      k_radix_hist<<<nblk, kSortThreads, 0, st>>>(kin, M, 8 * pass, nblk, hist);
-      k_scan_exclusive<<<1, 1024, 0, st>>>(hist, (int64_t)256 * nblk);
-      k_radix_scatter<<<nblk, kSortThreads, 0, st>>>(kin, vin, kout, vout, M, 8 * pass, nblk, hist);
+      k_radix_hist<<<nblk, kSortThreads, 0, st>>>(kin, M, 8 * pass, nblk, p->sort_hist);
+      k_scan_exclusive<<<1, 1024, 0, st>>>(p->sort_hist, (int64_t)256 * nblk);
+      k_radix_scatter<<<nblk, kSortThreads, 0, st>>>(kin, vin, kout, vout, M, 8 * pass, nblk, p->sort_hist);
       NUFFT_CUDA_TRY(p, cudaGetLastError());
       std::swap(kin, kout);
       std::swap(vin, vout);
@@ -634,14 +619,15 @@ int build_plan(nufft_plan_t* p, const float* om) {
       NUFFT_CUDA_TRY(p, cudaMemcpyAsync(p->perm, vin, M * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
     k_bin_start<<<(unsigned)((g.nbins + 1 + 255) / 256), 256, 0, st>>>(kin, M, g.nbins, p->bin_start);
     NUFFT_CUDA_TRY(p, cudaGetLastError());
-    NUFFT_CUDA_TRY(p, cudaStreamSynchronize(st));
   } else {
     NUFFT_CUDA_TRY(p, cudaMemsetAsync(p->bin_start, 0, (g.nbins + 1) * sizeof(int32_t), st));
   }
 
   // ---- gridding work list: each tile's points cut into chunks
   std::vector<int32_t> bs(g.nbins + 1);
-  NUFFT_CUDA_TRY(p, cudaMemcpy(bs.data(), p->bin_start, (g.nbins + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  NUFFT_CUDA_TRY(p, cudaMemcpyAsync(bs.data(), p->bin_start, (g.nbins + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                    st));
+  NUFFT_CUDA_TRY(p, cudaStreamSynchronize(st));
   std::vector<Chunk> ch;
   std::vector<int32_t> bc(g.nbins + 1);
   for (int64_t b = 0; b < g.nbins; ++b) {
@@ -656,73 +642,140 @@ int build_plan(nufft_plan_t* p, const float* om) {
     }
   }
   bc[g.nbins] = (int32_t)ch.size();
-  p->nchunks = (int64_t)ch.size();
-  NUFFT_CUDA_TRY(p, dalloc(p, &p->chunks, p->nchunks));
-  NUFFT_CUDA_TRY(p, dalloc(p, &p->bin_chunk, g.nbins + 1));
-  if (p->nchunks > 0)
-    NUFFT_CUDA_TRY(p, cudaMemcpy(p->chunks, ch.data(), ch.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
-  NUFFT_CUDA_TRY(p, cudaMemcpy(p->bin_chunk, bc.data(), bc.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  const int64_t nch = (int64_t)ch.size();
+  if (nch > p->chunk_cap) {   // grow the chunk list and the partial tiles (and the batched ones, lazily)
+    drop_graphs(p);
+    for (void* b : {(void*)p->chunks, (void*)p->tiles, (void*)p->btiles})
+      if (b) cudaFree(b);
+    p->device_bytes -= p->chunk_cap * ((int64_t)sizeof(Chunk) + g.padded_cells * (int64_t)sizeof(float2)) +
+                       (p->btiles ? (int64_t)p->batch_cap * p->chunk_cap * g.padded_cells * (int64_t)sizeof(float2) : 0);
+    p->chunks = nullptr;
+    p->tiles = nullptr;
+    if (p->btiles) {   // the other batched buffers are re-made with it
+      for (float2** b : {&p->bgrid, &p->bytmp, &p->bimg})
+        if (*b) { cudaFree(*b); *b = nullptr; }
+      p->device_bytes -= (int64_t)p->batch_cap * (p->Kprod + M + p->Nprod) * (int64_t)sizeof(float2);
+      p->btiles = nullptr;
+      p->batch_cap = 0;
+    }
+    p->chunk_cap = 0;
+    NUFFT_CUDA_TRY(p, dalloc(p, &p->chunks, nch));
+    NUFFT_CUDA_TRY(p, dalloc(p, &p->tiles, nch * g.padded_cells));
+    p->chunk_cap = nch;
+  }
+  p->nchunks = nch;
+  if (nch > 0)
+    NUFFT_CUDA_TRY(p, cudaMemcpyAsync(p->chunks, ch.data(), ch.size() * sizeof(Chunk), cudaMemcpyHostToDevice, st));
+  NUFFT_CUDA_TRY(p, cudaMemcpyAsync(p->bin_chunk, bc.data(), bc.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                    st));
 
   // ---- order the points of each chunk for conflict-free shared-memory atomics
-  if (M > 0 && p->nchunks > 0) {
-    int32_t* perm2 = nullptr;
-    NUFFT_CUDA_TRY(p, cudaMalloc((void**)&perm2, M * sizeof(int32_t)));
-    struct G2 { void* a; ~G2() { if (a) cudaFree(a); } } g2{perm2};
+  if (M > 0 && nch > 0) {
     const int cap = kChunkPoints[d];
     static_assert(kChunkPoints[1] < 32768 && kChunkPoints[2] < 32768 && kChunkPoints[3] < 32768,
                   "16-bit chunk positions");
     const size_t smem = (size_t)kBankWarps * cap * 5;
     if (smem > 48 * 1024)
       NUFFT_CUDA_TRY(p, cudaFuncSetAttribute(k_bank_order, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_bank_order<<<(unsigned)((p->nchunks + kBankWarps - 1) / kBankWarps), 32 * kBankWarps, smem, st>>>(
-        om, g, p->chunks, p->nchunks, p->perm, perm2, cap);
+    k_bank_order<<<(unsigned)((nch + kBankWarps - 1) / kBankWarps), 32 * kBankWarps, smem, st>>>(
+        om, g, p->chunks, nch, p->perm, p->perm2, cap);
     NUFFT_CUDA_TRY(p, cudaGetLastError());
-    NUFFT_CUDA_TRY(p, cudaMemcpyAsync(p->perm, perm2, M * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
-    NUFFT_CUDA_TRY(p, cudaStreamSynchronize(st));
+    NUFFT_CUDA_TRY(p, cudaMemcpyAsync(p->perm, p->perm2, M * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   }
 
   // ---- per-point interpolator in sorted order
-  int64_t coef_tot = 0;
-  for (int a = 0; a < d; ++a) { p->coef_off[a] = coef_tot; coef_tot += (int64_t)g.J[a] * M; }
-  NUFFT_CUDA_TRY(p, dalloc(p, &p->kf, M * d));
-  NUFFT_CUDA_TRY(p, dalloc(p, &p->coef, coef_tot));
-  NUFFT_CUDA_TRY(p, dalloc(p, &p->om_sorted, M * d));
   if (M > 0) {
-    // Chebyshev expansions of the coefficients in the offset delta, checked
-    // against the sums (kept for d c / d w too)
+    const DimTables D = dim_tables(p);
+    const int64_t n = M * d;
+    k_coefficients<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(om, 0, g, M, p->perm, p->s64, D, p->Tinv, p->kf,
+                                                               p->coef, p->coef_off[0], p->coef_off[1],
+                                                               p->coef_off[2], 0, p->om_sorted,
+                                                               p->cheb_ok[0] ? p->cheb : nullptr);
+    NUFFT_CUDA_TRY(p, cudaGetLastError());
+    if (p->dcoef) {
+      k_coefficients<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
+          p->om_sorted, 1, g, M, p->perm, p->s64, D, p->Tinv, nullptr, p->dcoef, p->coef_off[0], p->coef_off[1],
+          p->coef_off[2], 1, nullptr, p->cheb_ok[1] ? p->cheb : nullptr);
+      NUFFT_CUDA_TRY(p, cudaGetLastError());
+    }
+  }
+  return NUFFT_OK;
+}
+
+int build_plan(nufft_plan_t* p, const float* om) {
+  Geom& g = p->g;
+  const int d = g.d;
+  const int64_t M = p->M;
+  cudaStream_t st = p->stream;
+
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->flags, 2));
+  NUFFT_CUDA_TRY(p, cudaMemsetAsync(p->flags, 0, 2 * sizeof(int), st));
+  int rc = validate_om(p, om);
+  if (rc != NUFFT_OK) return rc;
+
+  // ---- per-dimension tables
+  int64_t s_tot = 0, tw_tot = 0, T_tot = 0;
+  for (int a = 0; a < d; ++a) {
+    p->s_off[a] = s_tot; p->tw_off[a] = tw_tot; p->T_off[a] = T_tot;
+    s_tot += g.N[a]; tw_tot += g.K[a]; T_tot += (int64_t)g.J[a] * g.J[a];
+  }
+  const DimTables D = dim_tables(p);
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->s, s_tot));
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->twiddle, tw_tot));
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->s64, s_tot));
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->Tinv, T_tot));
+  k_scaling_twiddle<<<d, 256, 0, st>>>(D, p->s, p->s64, p->twiddle);
+  NUFFT_CUDA_TRY(p, cudaGetLastError());
+  k_minmax_T<<<d, 256, 0, st>>>(D, p->s64, p->Tinv, p->flags + 1);
+  NUFFT_CUDA_TRY(p, cudaGetLastError());
+
+  // ---- Chebyshev expansions of the coefficients in the offset delta,
+  // checked against the sums (kept for d c / d w too)
+  int hflag[2] = {0, 0};
+  if (M > 0) {
     NUFFT_CUDA_TRY(p, dalloc(p, &p->cheb, (int64_t)d * 2 * kMaxJ * kCheb));
     double* err = nullptr;
     NUFFT_CUDA_TRY(p, cudaMalloc((void**)&err, 2 * kMaxDim * sizeof(double)));
     struct G5 { void* a; ~G5() { if (a) cudaFree(a); } } g5{err};
-    k_cheb_fit<<<2 * d, 64, 0, st>>>(D, s64, Tinv, p->cheb);
+    k_cheb_fit<<<2 * d, 64, 0, st>>>(D, p->s64, p->Tinv, p->cheb);
     NUFFT_CUDA_TRY(p, cudaGetLastError());
-    k_cheb_check<<<2 * d, 64, 0, st>>>(D, s64, Tinv, p->cheb, err);
+    k_cheb_check<<<2 * d, 64, 0, st>>>(D, p->s64, p->Tinv, p->cheb, err);
     NUFFT_CUDA_TRY(p, cudaGetLastError());
     double herr[2 * kMaxDim];
     NUFFT_CUDA_TRY(p, cudaMemcpyAsync(herr, err, 2 * d * sizeof(double), cudaMemcpyDeviceToHost, st));
+    NUFFT_CUDA_TRY(p, cudaMemcpyAsync(hflag, p->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     NUFFT_CUDA_TRY(p, cudaStreamSynchronize(st));
     p->cheb_ok[0] = p->cheb_ok[1] = 1;
     for (int a = 0; a < d; ++a)
       for (int v = 0; v < 2; ++v)
         if (!(herr[a * 2 + v] <= kChebTol)) p->cheb_ok[v] = 0;
-    const int64_t n = M * d;
-    k_coefficients<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(om, 0, g, M, p->perm, s64, D, Tinv, p->kf, p->coef,
-                                                               p->coef_off[0], p->coef_off[1], p->coef_off[2], 0,
-                                                               p->om_sorted, p->cheb_ok[0] ? p->cheb : nullptr);
-    NUFFT_CUDA_TRY(p, cudaGetLastError());
+  } else {
+    NUFFT_CUDA_TRY(p, cudaMemcpyAsync(hflag, p->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    NUFFT_CUDA_TRY(p, cudaStreamSynchronize(st));
   }
-  NUFFT_CUDA_TRY(p, cudaMemcpyAsync(hflag, flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-  NUFFT_CUDA_TRY(p, cudaStreamSynchronize(st));
   if (hflag[1]) return set_error(p, NUFFT_EINVAL, "min-max matrix G is singular for these sizes");
 
-  // ---- work space
-  NUFFT_CUDA_TRY(p, dalloc(p, &p->tiles, p->nchunks * g.padded_cells));
+  // ---- per-point arrays, sort scratch and work space
+  int64_t coef_tot = 0;
+  for (int a = 0; a < d; ++a) { p->coef_off[a] = coef_tot; coef_tot += (int64_t)g.J[a] * M; }
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->perm, M));
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->bin_start, g.nbins + 1));
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->bin_chunk, g.nbins + 1));
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->kf, M * d));
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->coef, coef_tot));
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->om_sorted, M * d));
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->sort_keys, 2 * M));
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->sort_vals, M));
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->sort_hist, M > 0 ? (int64_t)256 * sort_blocks(M) : 0));
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->perm2, M));
+  rc = build_points(p, om);
+  if (rc != NUFFT_OK) return rc;
   NUFFT_CUDA_TRY(p, dalloc(p, &p->grid, p->Kprod));
   NUFFT_CUDA_TRY(p, dalloc(p, &p->ytmp, M));
   NUFFT_CUDA_TRY(p, dalloc(p, &p->x_stage, p->Nprod));
   NUFFT_CUDA_TRY(p, dalloc(p, &p->y_stage, M));
-  rc = NUFFT_OK;
-  return rc;
+  NUFFT_CUDA_TRY(p, cudaStreamSynchronize(st));
+  return NUFFT_OK;
 }
 
 }  // namespace
@@ -914,6 +967,28 @@ extern "C" int nufft_plan_destroy(nufft_plan_t* p) {
 }
 
 extern "C" const char* nufft_last_error(const nufft_plan_t* p) { return p ? p->err : g_err; }
+
+extern "C" int nufft_plan_set_trajectory(nufft_plan_t* p, const float* om_dev) {
+  if (!p) return set_error(nullptr, NUFFT_EINVAL, "plan is NULL");
+  if (p->M > 0 && !om_dev) return set_error(p, NUFFT_EINVAL, "om_dev is NULL");
+  int rc = validate_om(p, om_dev);   // the plan is unchanged when this fails
+  if (rc != NUFFT_OK) return rc;
+  drop_graphs(p);                    // recorded launches carry the old chunk count
+  if (p->toep_T) {                   // the Toeplitz kernel belongs to the old trajectory
+    cudaFree(p->toep_T);
+    p->toep_T = nullptr;
+    if (p->toep_grid) cudaFree(p->toep_grid);
+    p->toep_grid = nullptr;
+    p->toep_cap = 0;
+    if (p->toep_geom) nufft_plan_destroy(p->toep_geom);
+    p->toep_geom = nullptr;
+    p->normal_op = 0;
+  }
+  rc = build_points(p, om_dev);
+  if (rc != NUFFT_OK) return rc;
+  NUFFT_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+  return NUFFT_OK;
+}
 
 extern "C" int nufft_set_stream(nufft_plan_t* p, void* stream) {
   if (!p) return set_error(nullptr, NUFFT_EINVAL, "plan is NULL");

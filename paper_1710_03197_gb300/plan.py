@@ -90,6 +90,19 @@ class NufftPlan:
     def set_stream(self, stream=None):
         check(lib.nufft_set_stream(self._h, _stream_ptr(stream)), self._h)
 
+    def set_trajectory(self, om: torch.Tensor):
+        """New trajectory of the same M points (C: nufft_plan_set_trajectory):
+        only the per-point interpolator and the tile sort are redone."""
+        if om.dim() == 1:
+            om = om[:, None]
+        if om.dim() != 2 or tuple(om.shape) != (self.M, self.d):
+            raise ValueError(f"om must have shape ({self.M}, {self.d})")
+        om = om.detach().to(torch.float32).contiguous()
+        self._sync_stream()
+        ptr = _dev_ptr(om, self.M * self.d, "om", dtype=torch.float32) if self.M > 0 else ctypes.c_void_p(0)
+        check(lib.nufft_plan_set_trajectory(self._h, ptr), self._h)
+        self._om = om
+
     def set_graphs(self, enable: bool):
         check(lib.nufft_set_graphs(self._h, 1 if enable else 0), self._h)
 
@@ -414,6 +427,10 @@ def nufft_plan(om, Nd, Kd, Jd, stream=None) -> NufftPlan:
 
 def nufft_plan_tuned(om, Nd, Kd, Jd, stream=None) -> NufftPlan:
     return NufftPlan(om, Nd, Kd, Jd, stream, autotune=True)
+
+
+def nufft_plan_set_trajectory(plan: NufftPlan, om) -> None:
+    plan.set_trajectory(om)
 
 
 def nufft_forward(plan: NufftPlan, x, y=None):
