@@ -156,7 +156,7 @@ WORKLOAD_TEXT = {
 
 
 def run_workload(nf, torch, name: str, steps: int, warmup: int, dev, flush_bytes: int, solvers: bool = False,
-                 extra_rows: bool = True):
+                 extra_rows: bool = True, autotune: bool = True):
     spec, om, x, noise = W.make_workload(name)
     M = spec["M"]
     om_d = torch.from_numpy(om).to(dev)
@@ -167,11 +167,12 @@ def run_workload(nf, torch, name: str, steps: int, warmup: int, dev, flush_bytes
     plan_ms = (time.perf_counter() - t0) * 1e3
     default_tile = plan.info()["tile_last"]
     plan.close()
-    # the timed steps use the autotuned plan (tile edge chosen by measurement)
+    # the timed steps use the autotuned plan (tile edge chosen by measurement);
+    # --no-autotune keeps the default plan (profiling runs: no candidate plans)
     t0 = time.perf_counter()
-    plan = nf.NufftPlan(om_d, spec["Nd"], spec["Kd"], spec["Jd"], autotune=True)
+    plan = nf.NufftPlan(om_d, spec["Nd"], spec["Kd"], spec["Jd"], autotune=autotune)
     torch.cuda.synchronize()
-    tuned_ms = (time.perf_counter() - t0) * 1e3
+    tuned_ms = (time.perf_counter() - t0) * 1e3 if autotune else None
     info = plan.info()
     xd = torch.from_numpy(x).to(dev)
     grid = torch.empty(spec["Kd"], dtype=torch.complex64, device=dev)
@@ -260,7 +261,7 @@ def run_workload(nf, torch, name: str, steps: int, warmup: int, dev, flush_bytes
     torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in evm]
 
-    rows = {"a1_plan_ms": round(plan_ms, 3), "a1_plan_tuned_ms": round(tuned_ms, 3),
+    rows = {"a1_plan_ms": round(plan_ms, 3), "a1_plan_tuned_ms": None if tuned_ms is None else round(tuned_ms, 3),
             "tile_edge": {"default": default_tile, "tuned": info["tile_last"]}}
     if extra_rows:
         rows.update(_extra_rows(plan, torch, spec, x, xd, xo, noise, steps, flush, stream, dev, solvers))
@@ -399,7 +400,8 @@ def ours(args):
     names = [w.strip() for w in args.workloads.split(",") if w.strip()]
     with ClockSampler(torch.cuda.current_device() if world == 1 else local, clocks_path) as clk:
         results = {n: run_workload(nf, torch, n, args.steps, args.warmup, dev, flush_bytes,
-                                   solvers=(i == 0 and not args.no_solvers), extra_rows=not args.no_rows)
+                                   solvers=(i == 0 and not args.no_solvers), extra_rows=not args.no_rows,
+                                   autotune=not args.no_autotune)
                    for i, n in enumerate(names)}
         next_rows = None
         if not args.no_solvers and not args.no_rows:
@@ -736,6 +738,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-solvers", action="store_true", help="skip the solver timings (rows a9)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="time the default plan instead of the tile-autotuned one (no candidate plans are built)")
     ap.add_argument("--no-rows", action="store_true",
                     help="time only the forward+adjoint step (no A^H A, Toeplitz, solver or extension rows)")
     ap.add_argument("--workloads", default="radial2d_256,kooshball3d_128",
