@@ -304,7 +304,7 @@ k_fft_pass(const FftArgs A, const int W) {
 
 // Lines per CTA: as many as give 256 threads (8 columns on a strided axis, for
 // 64-byte row segments), fewer when that would leave the GPU with fewer than
-// two CTAs per SM.
+// two CTAs per SM (counting every batch element's CTAs).
 constexpr int64_t kTargetBlocks = 2 * 152;
 
 template <int L, bool STRIDED, bool INV>
@@ -314,13 +314,13 @@ cudaError_t launch_L(const FftArgs& A, int nb, cudaStream_t st) {
   int64_t blocks;
   if (STRIDED) {
     W = 8;
-    while (W > 2 && (A.nouter * (A.inner / W) < kTargetBlocks ||
+    while (W > 2 && (A.nouter * (A.inner / W) * nb < kTargetBlocks ||
                      2 * SmemMap<L, STRIDED>::words(W) * sizeof(float2) > 96 * 1024))
       W >>= 1;
     blocks = A.nouter * (A.inner / W);
   } else {
     W = TPL >= 256 ? 1 : 256 / TPL;
-    while (W > 1 && (A.nouter + W - 1) / W < kTargetBlocks) W >>= 1;
+    while (W > 1 && (A.nouter + W - 1) / W * nb < kTargetBlocks) W >>= 1;
     blocks = (A.nouter + W - 1) / W;
   }
   const int threads = W * TPL;

@@ -143,13 +143,14 @@ def test_multicoil_rejects_bad_coil_shape(nf):
         assert nf.lib.nufft_forward_multicoil(plan.handle, None, 4, None, None) == 1     # EINVAL
 
 
+@pytest.mark.parametrize("nb", [5, 19])   # 19: batch groups of 8, 8 and 3 in the grouped kernels
 @pytest.mark.parametrize("name,Nd,Kd,Jd,gen", [
     ("2d", (32, 32), (64, 64), (6, 6), lambda: W.radial2d_golden(30, 64)),
+    ("2d_oddJ", (32, 32), (64, 64), (5, 7), lambda: W.uniform_random_om(1800, 2, seed=26)),
     ("3d", (16, 16, 16), (32, 32, 32), (6, 6, 6), lambda: W.kooshball3d(80, 32)),
 ])
-def test_batched_operators_equal_single_calls(nf, name, Nd, Kd, Jd, gen):
+def test_batched_operators_equal_single_calls(nf, name, Nd, Kd, Jd, gen, nb):
     om = gen()
-    nb = 5
     xs = cn((nb,) + Nd, 21)
     ys = cn((nb, om.shape[0]), 22)
     ref = oracle.make_plan(om, Nd, Kd, Jd)
