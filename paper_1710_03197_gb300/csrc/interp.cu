@@ -525,7 +525,9 @@ cudaError_t launch_reduce(const nufft_plan_t* p, const float2* tiles, float2* gr
   for (int a = 0; a < D; ++a) cells *= p->g.T[a];
   const int gsize = std::max(32, std::min(1024, cells / 4));
   if ((int64_t)gsize * 4 < cells) return cudaErrorInvalidValue;
-  const int NG = std::max(1, std::min(4, 1024 / gsize));   // groups splitting the chunk list
+  // groups splitting the chunk list; a batch (mostly sparse tiles, many CTAs)
+  // runs one group per CTA so that more tiles are in flight per SM
+  const int NG = nb > 1 ? 1 : std::max(1, std::min(4, 1024 / gsize));
   const size_t smem = NG > 1 ? (size_t)NG * 4 * gsize * sizeof(float2) : 0;
   k_gridding_reduce<D, 4><<<dim3((unsigned)p->g.nbins, (unsigned)nb), gsize * NG, smem, p->stream>>>(
       tiles, p->bin_chunk, grid, p->g, NG, p->nchunks * p->g.padded_cells, p->Kprod);
