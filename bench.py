@@ -393,8 +393,7 @@ def ours(args):
     import paper_1710_03197_gb300 as nf
 
     flush_bytes = 512 * 1024 * 1024
-    clocks_path = os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else None
+    clocks_path = args.clocks_csv   # optional copy of the raw nvidia-smi samples
     if world > 1:
         torch.distributed.barrier()
     names = [w.strip() for w in args.workloads.split(",") if w.strip()]
@@ -738,6 +737,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-solvers", action="store_true", help="skip the solver timings (rows a9)")
+    ap.add_argument("--clocks-csv", default=None,
+                    help="also write the raw nvidia-smi clock samples of the timed region to this file")
     ap.add_argument("--no-autotune", action="store_true",
                     help="time the default plan instead of the tile-autotuned one (no candidate plans are built)")
     ap.add_argument("--no-rows", action="store_true",
