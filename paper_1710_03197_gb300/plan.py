@@ -58,9 +58,11 @@ class NufftPlan:
         self._om = om
         h = ctypes.c_void_p(0)
         make = lib.nufft_plan_tuned if autotune else lib.nufft_plan   # autotune: tile edge by measurement
-        rc = make(d, _c_int_arr(Nd), _c_int_arr(Kd), _c_int_arr(Jd), M, om_ptr, _stream_ptr(stream), ctypes.byref(h))
+        sp = _stream_ptr(stream)
+        rc = make(d, _c_int_arr(Nd), _c_int_arr(Kd), _c_int_arr(Jd), M, om_ptr, sp, ctypes.byref(h))
         check(rc, None)
         self._h = h
+        self._stream_key = sp.value or 0
         self.d, self.M = d, M
         self.Nd, self.Kd, self.Jd = tuple(int(v) for v in Nd), tuple(int(v) for v in Kd), tuple(int(v) for v in Jd)
         self.device = om.device
@@ -88,7 +90,9 @@ class NufftPlan:
         self.close()
 
     def set_stream(self, stream=None):
-        check(lib.nufft_set_stream(self._h, _stream_ptr(stream)), self._h)
+        sp = _stream_ptr(stream)
+        check(lib.nufft_set_stream(self._h, sp), self._h)
+        self._stream_key = sp.value or 0
 
     def set_trajectory(self, om: torch.Tensor):
         """New trajectory of the same M points (C: nufft_plan_set_trajectory):
@@ -107,7 +111,12 @@ class NufftPlan:
         check(lib.nufft_set_graphs(self._h, 1 if enable else 0), self._h)
 
     def _sync_stream(self):
-        check(lib.nufft_set_stream(self._h, _stream_ptr()), self._h)
+        # order the plan's work on torch's current stream; the library keeps the
+        # stream it was last given, so the call is skipped when it is unchanged
+        s = torch.cuda.current_stream().cuda_stream
+        if s != self._stream_key:
+            check(lib.nufft_set_stream(self._h, ctypes.c_void_p(s)), self._h)
+            self._stream_key = s
 
     # ---------------------------------------------------------------- sizes
     @property
