@@ -135,6 +135,27 @@ def test_multicoil_cg_matches_oracle(nf):
     assert rel(x, X.cg_multicoil(ref, c128, y, np.zeros(Nd), 20)) < TOL_SOLVER
 
 
+def test_multicoil_full_size_frame_matches_oracle(nf):
+    """The batched multi-coil dynamic workload at its real size, one frame: the
+    first golden-angle frame of the series (256^2 image, 512^2 grid, J = 6x6)
+    with 4 of its coil maps; the normal operator (Eq. 33) and the adjoint of
+    the stacked coil data against the oracle."""
+    frames = W.dynamic_radial_frames(8, 512)
+    om = frames[0]
+    Nd, Kd = (256, 256), (512, 512)
+    nc = 4
+    coils = W.coil_maps(32, Nd)[:nc]
+    ref = oracle.make_plan(om, Nd, Kd, (6, 6))
+    x = W.ellipse_phantom(256)
+    y = cn(nc * om.shape[0], 31)
+    c128 = coils.astype(np.complex128)
+    with nf.NufftPlan(dev(om), Nd, Kd, (6, 6)) as plan:
+        cd = dev(coils)
+        got = host(plan.selfadjoint_multicoil(cd, dev(x)))
+        assert rel(got, X.selfadjoint_multicoil(ref, c128, x.astype(np.complex128))) < TOL_OP
+        assert rel(host(plan.adjoint_multicoil(cd, dev(y))), X.adjoint_multicoil(ref, c128, y)) < TOL_OP
+
+
 def test_multicoil_rejects_bad_coil_shape(nf):
     Nd, Kd, om, ref, coils = _multicoil_case()
     with nf.NufftPlan(dev(om), Nd, Kd, (6, 6)) as plan:
