@@ -125,7 +125,8 @@ const char* nufft_last_error(const nufft_plan_t* plan);
  * coefficients, and their trajectory derivative if the plan has computed it);
  * the scaling factors, the min-max inverses, their Chebyshev expansions and
  * the work space are kept, the chunk list and partial tiles grow when the new
- * points need more.  Recorded graphs are dropped (frame sets over the plan
+ * points need more, and the gridding tile edge stays (a tuned plan keeps its
+ * tuned edge).  Recorded graphs are dropped (frame sets over the plan
  * re-record), a Toeplitz kernel is discarded (the solvers' normal operator
  * goes back to V^H V until nufft_toeplitz_init is called again).
  * Synchronizes the stream.  Errors: NUFFT_EINVAL for a NULL argument or a
