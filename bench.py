@@ -329,36 +329,49 @@ def _extra_rows(plan, torch, spec, x, xd, xo, noise, steps, flush, stream, dev, 
         rows[key] = round(statistics.mean(t_), 5)
     del gfull
     if solvers:
-        # the reconstruction runs of the paper's solvers on this workload's data
+        # the reconstruction runs of the paper's solvers on this workload's
+        # data.  Each solve runs three times on the same buffers (reset to the
+        # start value): the first call launches eagerly, the second records
+        # the library's graph, the third replays it and is the reported time;
+        # the first is reported beside it as *_eager_ms.
         yd = plan.forward(xd)
         if noise is not None:
             yd = yd + torch.from_numpy(noise).to(dev)
         yd = yd.contiguous()
-        x0 = torch.zeros(spec["Nd"], dtype=torch.complex64, device=dev)
-        plan.solve_cg(yd, x0.clone(), maxiter=2)
-        for key, fn in (("a9_cg_100_iterations_ms", lambda: plan.solve_cg(yd, x0.clone(), maxiter=100)),
-                        ("a9_l1tv_ols_50_iterations_ms",
-                         lambda: plan.solve_l1tv_ols(yd, x0.clone(), maxiter=50, inner=2, cg_iters=5, mu=1.0, lam=0.01)),
-                        ("a9_l1tv_lad_50_iterations_ms",
-                         lambda: plan.solve_l1tv_lad(yd, x0.clone(), maxiter=50, inner=2, cg_iters=5, mu=1.0, lam=0.01))):
-            torch.cuda.synchronize()
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            e1.synchronize()
-            rows[key] = round(e0.elapsed_time(e1), 3)
+        xb = torch.zeros(spec["Nd"], dtype=torch.complex64, device=dev)
+        wb = torch.ones(plan.M, dtype=torch.float32, device=dev)
+
+        def timed(key, fn, reset):
+            t_ = []
+            for _ in range(3):
+                reset()
+                torch.cuda.synchronize()
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                t_.append(e0.elapsed_time(e1))
+            rows[key] = round(t_[-1], 3)
+            rows[key.replace("_ms", "_eager_ms")] = round(t_[0], 3)
+
+        zero_x = xb.zero_
+        timed("a9_cg_100_iterations_ms", lambda: plan.solve_cg(yd, xb, maxiter=100), zero_x)
+        timed("a9_l1tv_ols_50_iterations_ms",
+              lambda: plan.solve_l1tv_ols(yd, xb, maxiter=50, inner=2, cg_iters=5, mu=1.0, lam=0.01), zero_x)
+        timed("a9_l1tv_lad_50_iterations_ms",
+              lambda: plan.solve_l1tv_lad(yd, xb, maxiter=50, inner=2, cg_iters=5, mu=1.0, lam=0.01), zero_x)
         rows["a9_solver_settings"] = "CG x0=0; L1TV: inner=2, cg_iters=5, mu=1, lambda=0.01"
+        # density compensation (Pipe-Menon, 5 iterations from w = 1) and the
+        # gridding reconstruction A^H (y w); the paper's k-space CG (20 steps)
+        timed("f3_density_compensation_5_iterations_ms", lambda: plan.density_compensation(5, wb),
+              lambda: wb.fill_(1.0))
+        timed("f3_gridding_recon_ms", lambda: plan.gridding_recon(yd, wb, xb), lambda: None)
+        timed("f4_cg_kspace_20_iterations_ms", lambda: plan.solve_cg_kspace(yd, xb, maxiter=20), lambda: None)
         # the same solves with the Toeplitz normal operator
         plan.set_normal_operator(True)
-        for key, fn in (("f4_cg_100_iterations_toeplitz_ms", lambda: plan.solve_cg(yd, x0.clone(), maxiter=100)),
-                        ("f4_l1tv_ols_50_iterations_toeplitz_ms",
-                         lambda: plan.solve_l1tv_ols(yd, x0.clone(), maxiter=50, inner=2, cg_iters=5, mu=1.0, lam=0.01))):
-            torch.cuda.synchronize()
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            e1.synchronize()
-            rows[key] = round(e0.elapsed_time(e1), 3)
+        timed("f4_cg_100_iterations_toeplitz_ms", lambda: plan.solve_cg(yd, xb, maxiter=100), zero_x)
+        timed("f4_l1tv_ols_50_iterations_toeplitz_ms",
+              lambda: plan.solve_l1tv_ols(yd, xb, maxiter=50, inner=2, cg_iters=5, mu=1.0, lam=0.01), zero_x)
         plan.set_normal_operator(False)
     return rows
 
