@@ -953,14 +953,28 @@ extern "C" int nufft_plan_tuned(int d, const int* Nd, const int* Kd, const int* 
   return NUFFT_OK;
 }
 
+// Free the Toeplitz kernel, its work grid and its geometry plan.  The geometry
+// plan is handed the owner's stream first: it last ran on whatever stream the
+// owner used then (possibly the owner's capture stream, destroyed after this).
+static void release_toeplitz(nufft_plan_t* p) {
+  if (p->toep_geom) {
+    p->toep_geom->stream = p->stream;
+    nufft_plan_destroy(p->toep_geom);
+    p->toep_geom = nullptr;
+  }
+  if (p->toep_T) cudaFree(p->toep_T);
+  if (p->toep_grid) cudaFree(p->toep_grid);
+  p->toep_T = nullptr;
+  p->toep_grid = nullptr;
+  p->toep_cap = 0;
+}
+
 extern "C" int nufft_plan_destroy(nufft_plan_t* p) {
   if (!p) return NUFFT_OK;
   cudaStreamSynchronize(p->stream);
   drop_graphs(p);
+  release_toeplitz(p);   // before the capture stream, which its geometry plan may still name
   if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
-  if (p->toep_geom) nufft_plan_destroy(p->toep_geom);
-  if (p->toep_T) cudaFree(p->toep_T);
-  if (p->toep_grid) cudaFree(p->toep_grid);
   free_plan_memory(p);
   delete p;
   return NUFFT_OK;
@@ -975,13 +989,7 @@ extern "C" int nufft_plan_set_trajectory(nufft_plan_t* p, const float* om_dev) {
   if (rc != NUFFT_OK) return rc;
   drop_graphs(p);                    // recorded launches carry the old chunk count
   if (p->toep_T) {                   // the Toeplitz kernel belongs to the old trajectory
-    cudaFree(p->toep_T);
-    p->toep_T = nullptr;
-    if (p->toep_grid) cudaFree(p->toep_grid);
-    p->toep_grid = nullptr;
-    p->toep_cap = 0;
-    if (p->toep_geom) nufft_plan_destroy(p->toep_geom);
-    p->toep_geom = nullptr;
+    release_toeplitz(p);
     p->normal_op = 0;
   }
   rc = build_points(p, om_dev);

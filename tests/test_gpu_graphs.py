@@ -201,3 +201,39 @@ def test_host_buffer_calls_replay_with_new_contents(nf, pinned):
         plan.adjoint_host(y_h, xo_h)
         assert rel(xo_h.numpy(), oracle.adjoint(ref, y)) < 2e-5
     plan.close()
+
+
+@pytest.mark.parametrize("then", ["close", "set_trajectory"])
+def test_recorded_toeplitz_solve_leaves_no_cuda_error(nf, then):
+    """A CG solve on the Toeplitz normal operator run eagerly, recorded and
+    replayed on the same buffers, then the plan closed (or moved to a new
+    trajectory, which discards the Toeplitz kernel): the library's next calls,
+    on this plan or a new one, meet no leftover CUDA error."""
+    Nd, Kd, Jd = (32, 32), (64, 64), (6, 6)
+    om = W.uniform_random_om(1000, 2, seed=41)
+    om2 = W.uniform_random_om(1000, 2, seed=44)
+    y = dev(cn(1000, 42))
+    plan = nf.NufftPlan(dev(om), Nd, Kd, Jd)
+    plan.toeplitz_init()
+    plan.set_normal_operator(True)
+    x = torch.zeros(Nd, dtype=torch.complex64, device=DEV)
+    for _ in range(3):
+        x.zero_()
+        plan.solve_cg(y, x, maxiter=5)
+    torch.cuda.synchronize()
+    xx = cn(Nd, 43)
+    if then == "close":
+        plan.close()
+        with nf.NufftPlan(dev(om2), Nd, Kd, Jd) as p2:
+            got = p2.forward(dev(xx))
+            torch.cuda.synchronize()
+            assert rel(got.cpu().numpy(), oracle.forward(oracle.make_plan(om2, Nd, Kd, Jd), xx)) < 2e-5
+    else:
+        plan.set_trajectory(dev(om2))
+        got = plan.forward(dev(xx))
+        torch.cuda.synchronize()
+        assert rel(got.cpu().numpy(), oracle.forward(oracle.make_plan(om2, Nd, Kd, Jd), xx)) < 2e-5
+        with nf.NufftPlan(dev(om), Nd, Kd, Jd) as p2:
+            p2.forward(dev(xx))
+            torch.cuda.synchronize()
+        plan.close()
