@@ -55,6 +55,9 @@ def test_calls_reject_null_plan():
     assert L.solve_cg(null, x, x, 3) == EINVAL
     assert L.solve_l1tv_ols(null, x, x, 1, 1, 1, 1.0, 1.0) == EINVAL
     assert L.solve_l1tv_lad(null, x, x, 1, 1, 1, 1.0, 1.0) == EINVAL
+    for name in ["nufft_trajectory_gradient", "nufft_trajectory_gradient_grid"]:
+        assert getattr(L, name)(null, x, x, x) == EINVAL, name
+    assert L.nufft_plan_set_trajectory(null, x) == EINVAL
     assert L.nufft_set_stream(null, None) == EINVAL
     assert L.nufft_plan_info(null, None) == EINVAL
     assert L.nufft_plan_destroy(null) == 0
