@@ -16,9 +16,11 @@ primitives used as single steps: ``numpy.fft.fftn``/``ifftn`` (the FFT),
 
 Pins: every function is checked in ``tests/test_oracle_pins.py`` against
 brute-force NUDFT, the adjoint identity, closed forms, least-squares
-definitions solved by LAPACK, and dense solves.  The L1TV-OLS and L1TV-LAD
-outer loops are "parity unpinned" beyond their component pins (gradient,
-shrink, the inner K-solve and the lambda -> 0 reduction).
+definitions solved by LAPACK, and dense solves; the L1TV-OLS and L1TV-LAD
+outer (Bregman) loops are pinned in ``tests/test_oracle_pins_l1tv.py`` to the
+limit the constrained problem fixes (x_true for full-rank consistent data, a
+feasible TV minimiser for underdetermined data), with planted mistakes in
+their update lines failing those pins.
 """
 from .minmax import kb_scaling_1d, offsets_1d, minmax_G, minmax_r, minmax_coefficients_1d
 from .nufft import Plan, make_plan, forward, adjoint, selfadjoint, nudft_forward, nudft_adjoint

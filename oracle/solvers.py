@@ -26,6 +26,11 @@ Readings (the paper leaves these open):
 * TV is anisotropic (sum over axes of |grad_i x|), with every axis of the
   image used (x, y and, in 3D, z).
 * CG guards: alpha = 0 when <p, A p> = 0, beta = 0 when <r, r> = 0.
+
+Pins: the Bregman loops of ``l1tv_ols`` and ``l1tv_lad`` converge to a
+solution of min TV(x) subject to A x = y; ``tests/test_oracle_pins_l1tv.py``
+checks that limit on full-rank and underdetermined problems with the shrink
+active.
 """
 from __future__ import annotations
 
