@@ -152,6 +152,8 @@ WORKLOAD_TEXT = {
     "kooshball3d_128": "kooshball3d_128: 3D 128^3 image, 256^3 grid, J=6^3, kooshball 8192 Fibonacci spokes x 256 "
                        "samples (2,097,152 points), complex normal image",
     "radial2d_64": "radial2d_64: 2D 64x64 image, 128x128 grid, J=6x6, 64 uniform spokes x 128 samples (8192 points)",
+    "radial2d_256_K384": "radial2d_256_K384: the radial2d_256 image and trajectory on a 1.5x oversampled 384x384 "
+                         "grid (mixed-radix FFT passes, radix 3), J=6x6, 206,336 points",
 }
 
 
@@ -421,32 +423,28 @@ def ours(args):
                          "f2_differentiable_spiral": run_differentiable(nf, torch, dev)}
     torch.cuda.synchronize()
     res2 = results[names[0]]
-    res3 = results[names[1]] if len(names) > 1 else None
 
     M2 = res2["spec"]["M"]
     tot_ms = sum(res2["step_ms"])
     elapsed, units = reduce_over_ranks(tot_ms * 1e-3, M2 * args.steps, world)
     value = units / elapsed
     e2e_el, e2e_units = reduce_over_ranks(res2["e2e_s"] * args.steps, M2 * args.steps, world)
-    if res3 is not None:
-        M3 = res3["spec"]["M"]
-        el3, un3 = reduce_over_ranks(sum(res3["step_ms"]) * 1e-3, M3 * args.steps, world)
+    others = {}
+    for n in names[1:]:
+        r = results[n]
+        others[n] = (r, reduce_over_ranks(sum(r["step_ms"]) * 1e-3, r["spec"]["M"] * args.steps, world))
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return
 
     peak, peak_kind = load_peaks()
-    traffic = {}
+    traffic_all = {}
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
         with open(tpath) as f:
             traffic_all = json.load(f)
-        traffic = traffic_all.get(names[0], {})
-        traffic3 = traffic_all.get(names[1], {}) if res3 is not None else {}
-    else:
-        traffic3 = {}
-    dom2, stages2, roof2 = roofline_for(res2, peak, peak_kind, traffic)
+    dom2, stages2, roof2 = roofline_for(res2, peak, peak_kind, traffic_all.get(names[0], {}))
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -472,16 +470,18 @@ def ours(args):
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }
-    if res3 is not None:
-        dom3, stages3, roof3 = roofline_for(res3, peak, peak_kind, traffic3)
-        line["also"] = {names[1]: {
-            "workload": WORKLOAD_TEXT[names[1]],
-            "value": round(un3 / el3, 1), "unit": UNIT, "ms_per_step": round(el3 * 1e3 / args.steps, 5),
-            "e2e": {"value": round(M3 / res3["e2e_s"], 1), "unit": UNIT, "h2d_bytes_per_step": res3["h2d"],
-                    "d2h_bytes_per_step": res3["d2h"]},
-            "gpu_launches": launches_per_step(res3["spec"], res3["info"]["nchunks"]) * args.steps,
-            "roofline": roof3, "stages": stages3, "rows": res3["rows"],
-            "staged_ms_per_step": round(statistics.mean(res3["staged_ms"]), 5)}}
+    if others:
+        line["also"] = {}
+        for n, (r, (el_n, un_n)) in others.items():
+            _, stages_n, roof_n = roofline_for(r, peak, peak_kind, traffic_all.get(n, {}))
+            line["also"][n] = {
+                "workload": WORKLOAD_TEXT[n],
+                "value": round(un_n / el_n, 1), "unit": UNIT, "ms_per_step": round(el_n * 1e3 / args.steps, 5),
+                "e2e": {"value": round(r["spec"]["M"] / r["e2e_s"], 1), "unit": UNIT,
+                        "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
+                "gpu_launches": launches_per_step(r["spec"], r["info"]["nchunks"]) * args.steps,
+                "roofline": roof_n, "stages": stages_n, "rows": r["rows"],
+                "staged_ms_per_step": round(statistics.mean(r["staged_ms"]), 5)}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -756,8 +756,8 @@ def main(argv=None):
                     help="time the default plan instead of the tile-autotuned one (no candidate plans are built)")
     ap.add_argument("--no-rows", action="store_true",
                     help="time only the forward+adjoint step (no A^H A, Toeplitz, solver or extension rows)")
-    ap.add_argument("--workloads", default="radial2d_256,kooshball3d_128",
-                    help="comma list; the first sets value/roofline, the second is reported under 'also'")
+    ap.add_argument("--workloads", default="radial2d_256,kooshball3d_128,radial2d_256_K384",
+                    help="comma list; the first sets value/roofline, the others are reported under 'also'")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)           # at least 3 untimed warm-up steps
     if args.impl == "reference":

@@ -79,7 +79,13 @@ typedef struct nufft_plan nufft_plan_t;
  *
  *   d       number of dimensions, 1..3
  *   Nd      image size per dimension (d ints): even, 2 <= N_i <= K_i
- *   Kd      oversampled grid per dimension (d ints): a power of two, 16..1024
+ *   Kd      oversampled grid per dimension (d ints): even, 16..1024, with no
+ *           prime factor other than 2, 3 and 5 (e.g. 1.25x / 1.5x grids such
+ *           as 80, 320, 384); powers of two take the register-resident FFT
+ *           passes, the other sizes a mixed-radix pass through shared memory.
+ *           The gridding tile edge is the largest divisor of K_i up to 16
+ *           (2D, 3D) or 1024 (1D), or, if that is below J_i - 1, the smallest
+ *           divisor of K_i from J_i - 1 up.
  *   Jd      neighbours per dimension (d ints): 1 <= J_i <= 16
  *   M       number of k-space points, 0 <= M < 2^31
  *   om_dev  M x d float32 device array (may be NULL when M == 0); every value
@@ -221,9 +227,12 @@ int nufft_ifft_crop_rescale(nufft_plan_t* plan, float* grid_dev, float* x_dev);
  * frees nothing.  Plans whose partial tiles need more than 16 MiB
  * (nchunks * padded-tile bytes, nufft_plan_info [12]) are rejected with
  * NUFFT_EINVAL; the 2D 256^2 / 512^2 workloads fit, large 3D grids do not.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current): make that first call before any stream
- * capture.  Every call shares the one array, and each call overwrites the
+ * The call runs on the plan's device (the device current when the plan was
+ * made): it makes that device current for its duration and restores the
+ * caller's current device before returning.  The first call on a device looks
+ * up the array's device address there (once per device, with that device
+ * current): make that first call before any stream capture.  Every call
+ * shares the one array, and each call overwrites the
  * part it uses before reading it, so nothing needs clearing; calls that can
  * overlap on the GPU (other streams, other plans, other threads) race on it
  * and must be serialised by the caller.
@@ -405,6 +414,23 @@ int nufft_trajectory_gradient(nufft_plan_t* plan, const float* x_dev, const floa
  * nufft_scale_pad_fft(x).
  */
 int nufft_trajectory_gradient_grid(nufft_plan_t* plan, const float* grid_dev, const float* g_dev, float* gom_dev);
+
+/*
+ * Fault injection for tests (no counterpart in the paper).  Every device
+ * buffer the library owns is allocated through one wrapper.
+ *
+ * nufft_debug_fail_allocation - arm a one-shot failure: the n-th device
+ *   allocation the library makes from now on (n = 0: the next one) fails as
+ *   if the device were out of memory, without calling CUDA, so the call that
+ *   makes it returns NUFFT_ENOMEM and no CUDA error is left behind.  n < 0
+ *   disarms.  Process-wide; returns NUFFT_OK.
+ * nufft_debug_device_bytes - bytes of device memory the library holds now,
+ *   over all plans, frame sets and work spaces (the static scratch of
+ *   nufft_gridding_static not included).  A call that fails must leave this
+ *   where it was before the call, apart from work space it keeps by design.
+ */
+int nufft_debug_fail_allocation(int64_t n);
+int64_t nufft_debug_device_bytes(void);
 
 #ifdef __cplusplus
 }

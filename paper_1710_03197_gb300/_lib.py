@@ -76,6 +76,8 @@ _SIGS = {
     "nufft_toeplitz_init": (_i, [_PLAN]),
     "nufft_selfadjoint_toeplitz": (_i, [_PLAN, _vp, _vp]),
     "nufft_set_normal_operator": (_i, [_PLAN, _i]),
+    "nufft_debug_fail_allocation": (_i, [_i64]),
+    "nufft_debug_device_bytes": (_i64, []),
 }
 
 for _name, (_res, _args) in _SIGS.items():

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnufft_gb300.so")
-SOURCES = ["plan.cu", "fft.cu", "interp.cu", "capi.cu", "solvers.cu", "recon.cu", "grad.cu", "toeplitz.cu", "graphs.cu", "frames.cu"]
+SOURCES = ["plan.cu", "fft.cu", "interp.cu", "capi.cu", "solvers.cu", "recon.cu", "grad.cu", "toeplitz.cu", "graphs.cu", "frames.cu", "memory.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

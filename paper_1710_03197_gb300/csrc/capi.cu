@@ -58,15 +58,27 @@ int ensure_batch(nufft_plan_t* p, int nb) {
   if (nb <= p->batch_cap) return NUFFT_OK;
   drop_graphs(p);   // graphs may reference the buffers freed below
   for (float2** b : {&p->bgrid, &p->btiles, &p->bytmp, &p->bimg})
-    if (*b) { cudaFree(*b); *b = nullptr; }
+    if (*b) { dev_free(*b); *b = nullptr; }
+  p->device_bytes -= (int64_t)p->batch_cap *
+                     (p->Kprod + p->chunk_cap * p->g.padded_cells + (p->M > 0 ? p->M : 1) + p->Nprod) *
+                     (int64_t)sizeof(float2);
   p->batch_cap = 0;
   const int64_t counts[4] = {(int64_t)nb * p->Kprod, (int64_t)nb * p->chunk_cap * p->g.padded_cells,
                              (int64_t)nb * (p->M > 0 ? p->M : 1), (int64_t)nb * p->Nprod};
   float2** bufs[4] = {&p->bgrid, &p->btiles, &p->bytmp, &p->bimg};
   for (int k = 0; k < 4; ++k) {
     if (counts[k] == 0) continue;
-    cudaError_t e = cudaMalloc((void**)bufs[k], counts[k] * sizeof(float2));
-    if (e != cudaSuccess) { *bufs[k] = nullptr; return cuda_check(p, e, "batched work space"); }
+    cudaError_t e = dev_malloc((void**)bufs[k], counts[k] * sizeof(float2));
+    if (e != cudaSuccess) {   // release what this call took; the plan keeps no batch capacity
+      for (int q = 0; q < k; ++q)
+        if (*bufs[q]) {
+          dev_free(*bufs[q]);
+          *bufs[q] = nullptr;
+          p->device_bytes -= counts[q] * (int64_t)sizeof(float2);
+        }
+      *bufs[k] = nullptr;
+      return cuda_check(p, e, "batched work space");
+    }
     p->device_bytes += counts[k] * (int64_t)sizeof(float2);
   }
   p->batch_cap = nb;

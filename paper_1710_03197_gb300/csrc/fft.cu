@@ -16,13 +16,15 @@
 //     the last pass (last axis) applies S^H and writes the image.
 // Padded position of image index n along an axis: g = (n - N/2) mod K.
 //
-// Each line is transformed by a Stockham auto-sort FFT (mixed radix: one
-// radix-2 or radix-4 stage, then radix-8 stages), each thread holding 8 values
-// per stage in registers.  The first stage works on the values as loaded and
+// Each line of power-of-two length is transformed by a Stockham auto-sort
+// FFT (one radix-2 or radix-4 stage, then radix-8 stages), each thread
+// holding 8 values per stage in registers.  The first stage works on the values as loaded and
 // the last stage's outputs are stored as they are; the hand-offs between
 // stages go through two shared-memory buffers used in turn, one barrier per
 // hand-off.  Twiddles exp(-2 pi i k / K) come from a table computed in FP64 at
 // plan time and are loaded before the barrier of the stage that uses them.
+// Other line lengths (even, prime factors 2, 3 and 5) run a Stockham FFT of
+// radix-8, -4/-2, -3 and -5 stages through shared memory (k_fft_mixed).
 #include "internal.cuh"
 
 namespace nufft {
@@ -217,7 +219,7 @@ k_fft_pass(const FftArgs A, const int W) {
     for (int i = A.a - 1; i >= 0; --i) {
       const int n = (int)(rem % A.lead_N[i]);
       rem /= A.lead_N[i];
-      const int gi = (n - A.lead_N[i] / 2 + A.lead_K[i]) & (A.lead_K[i] - 1);
+      const int gi = wrapk(n - A.lead_N[i] / 2 + A.lead_K[i], A.lead_K[i]);
       goff += (int64_t)gi * A.lead_stride[i];
       if (A.scale && (A.src_image || A.dst_image)) slead *= A.s_lead[i][n];
     }
@@ -314,7 +316,7 @@ cudaError_t launch_L(const FftArgs& A, int nb, cudaStream_t st) {
   int64_t blocks;
   if (STRIDED) {
     W = 8;
-    while (W > 2 && (A.nouter * (A.inner / W) * nb < kTargetBlocks ||
+    while (W > 2 && (A.inner % W != 0 || A.nouter * (A.inner / W) * nb < kTargetBlocks ||
                      2 * SmemMap<L, STRIDED>::words(W) * sizeof(float2) > 96 * 1024))
       W >>= 1;
     blocks = A.nouter * (A.inner / W);
@@ -335,6 +337,236 @@ cudaError_t launch_L(const FftArgs& A, int nb, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------- other line lengths
+// Stockham FFT of a line of length L = 2^a 3^b 5^c through shared memory:
+// radix-8 stages, one radix-4 or radix-2 stage, then radix-3 and radix-5
+// stages.  Stage s of radix R and span Ns (the product of the earlier radices)
+// takes butterfly j (0 <= j < L/R) from elements j + r L/R, multiplies input
+// r by exp(-+ 2 pi i r k / (Ns R)), k = j mod Ns, transforms the R values and
+// writes output r to (j - k) R + k + r Ns.  The line sits in shared memory
+// (two buffers used in turn, one barrier per stage); loads and stores are
+// pruned and scaled as in k_fft_pass.
+constexpr int kMaxStages = 16;
+struct MixedRadix {
+  int L;
+  int nst;
+  int radix[kMaxStages];
+};
+
+MixedRadix mixed_radix(int L) {
+  MixedRadix m;
+  memset(&m, 0, sizeof(m));
+  m.L = L;
+  int a = 0, v = L;
+  while (v % 2 == 0) { v /= 2; ++a; }
+  for (int i = 0; i < a / 3; ++i) m.radix[m.nst++] = 8;
+  if (a % 3 == 2) m.radix[m.nst++] = 4;
+  if (a % 3 == 1) m.radix[m.nst++] = 2;
+  while (v % 3 == 0) { v /= 3; m.radix[m.nst++] = 3; }
+  while (v % 5 == 0) { v /= 5; m.radix[m.nst++] = 5; }
+  if (v != 1) m.nst = -1;   // not a supported length
+  return m;
+}
+
+// DFT of 3 points: with w = exp(-+ 2 pi i / 3), y1 = v0 + w v1 + w^2 v2 and
+// y2 = v0 + w^2 v1 + w v2 split into (v0 - (v1 + v2) / 2) -+ i (sqrt 3 / 2)(v1 - v2).
+template <bool INV>
+__device__ __forceinline__ void dft3(float2* v) {
+  const float h = 0.86602540378443864676f;   // sqrt(3) / 2
+  const float2 t1 = cadd(v[1], v[2]);
+  const float2 t2 = make_float2(v[0].x - 0.5f * t1.x, v[0].y - 0.5f * t1.y);
+  const float2 t3 = rot90<INV>(cscale(csub(v[1], v[2]), h));
+  v[0] = cadd(v[0], t1);
+  v[1] = cadd(t2, t3);
+  v[2] = csub(t2, t3);
+}
+
+// DFT of 5 points: with c_k = cos(2 pi k / 5), s_k = sin(2 pi k / 5),
+// y1, y4 = v0 + c1 (v1 + v4) + c2 (v2 + v3) -+ i (s1 (v1 - v4) + s2 (v2 - v3)),
+// y2, y3 = v0 + c2 (v1 + v4) + c1 (v2 + v3) -+ i (s2 (v1 - v4) - s1 (v2 - v3)).
+template <bool INV>
+__device__ __forceinline__ void dft5(float2* v) {
+  const float c1 = 0.30901699437494742410f, c2 = -0.80901699437494742410f;
+  const float s1 = 0.95105651629515357212f, s2 = 0.58778525229247312917f;
+  const float2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+  const float2 t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+  const float2 a1 = make_float2(v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y);
+  const float2 a2 = make_float2(v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y);
+  const float2 b1 = rot90<INV>(make_float2(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y));
+  const float2 b2 = rot90<INV>(make_float2(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y));
+  v[0] = make_float2(v[0].x + t1.x + t2.x, v[0].y + t1.y + t2.y);
+  v[1] = cadd(a1, b1);
+  v[4] = csub(a1, b1);
+  v[2] = cadd(a2, b2);
+  v[3] = csub(a2, b2);
+}
+
+template <bool STRIDED>
+struct MixedMap {
+  int w, L;   // lines per CTA, line length
+  __device__ __forceinline__ int at(int b, int p) const { return STRIDED ? p * (w + 1) + b : b * (L + 1) + p; }
+  __host__ __device__ static size_t words(int w, int L) { return (size_t)(STRIDED ? L * (w + 1) : w * (L + 1)); }
+};
+
+template <int R, bool INV, bool STRIDED>
+__device__ __forceinline__ void mixed_stage(const float2* __restrict__ src, float2* __restrict__ dst,
+                                            const MixedMap<STRIDED> SI, int b, int t, int TPL, int Ns,
+                                            const float2* __restrict__ tw) {
+  const int L = SI.L;
+  const int nbf = L / R;
+  const int step = L / (Ns * R);
+  for (int j = t; j < nbf; j += TPL) {
+    const int k = j % Ns;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[SI.at(b, j + r * nbf)];
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        float2 w = __ldg(&tw[r * k * step]);
+        if (INV) w.y = -w.y;
+        v[r] = cmul(v[r], w);
+      }
+    }
+    if (R == 3) dft3<INV>(v);
+    else if (R == 5) dft5<INV>(v);
+    else dft<R, INV>(v);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[SI.at(b, base + r * Ns)] = v[r];
+  }
+}
+
+template <bool STRIDED, bool INV>
+__global__ void __launch_bounds__(256)
+k_fft_mixed(const FftArgs A, const int W, const __grid_constant__ MixedRadix mr) {
+  const int L = mr.L;
+  const int TPL = blockDim.x / W;
+  const MixedMap<STRIDED> SI{W, L};
+  extern __shared__ float2 sm[];
+  const int bufw = (int)MixedMap<STRIDED>::words(W, L);
+
+  const int tid = threadIdx.x;
+  int b, t;
+  int64_t o, in;
+  if (STRIDED) {
+    b = tid % W;
+    t = tid / W;
+    const int64_t nib = A.inner / W;
+    o = blockIdx.x / nib;
+    in = (blockIdx.x % nib) * W + b;
+  } else {
+    b = tid / TPL;
+    t = tid % TPL;
+    o = (int64_t)blockIdx.x * W + b;
+    in = 0;
+  }
+  const bool live = o < A.nouter;
+  const float2* __restrict__ src = A.src + (int64_t)blockIdx.y * A.src_bstride;
+  float2* __restrict__ dst = A.dst + (int64_t)blockIdx.y * A.dst_bstride;
+
+  int64_t goff = 0;
+  float slead = 1.0f;
+  if (live) {
+    int64_t rem = o;
+    for (int i = A.a - 1; i >= 0; --i) {
+      const int n = (int)(rem % A.lead_N[i]);
+      rem /= A.lead_N[i];
+      const int gi = wrapk(n - A.lead_N[i] / 2 + A.lead_K[i], A.lead_K[i]);
+      goff += (int64_t)gi * A.lead_stride[i];
+      if (A.scale && (A.src_image || A.dst_image)) slead *= A.s_lead[i][n];
+    }
+  }
+  const int half = A.Na >> 1;
+  const int64_t stride = A.inner;
+
+  for (int p = t; p < L; p += TPL) {
+    float2 v = make_float2(0.f, 0.f);
+    if (live) {
+      if (!INV) {
+        if ((p < half) || (p >= L - half)) {
+          if (A.src_image) {
+            const int n = p < half ? p + half : p - L + half;
+            v = cscale(__ldg(&src[o * A.Na + n]), (A.scale ? A.s_axis[n] : 1.0f) * slead);
+          } else {
+            v = src[goff + (int64_t)p * stride + in];
+          }
+        }
+      } else {
+        v = src[goff + (int64_t)p * stride + in];
+      }
+    }
+    sm[SI.at(b, p)] = v;
+  }
+  __syncthreads();
+
+  int cur = 0, Ns = 1;
+  for (int s = 0; s < mr.nst; ++s) {
+    const int R = mr.radix[s];
+    const float2* in_buf = sm + cur * bufw;
+    float2* out_buf = sm + (cur ^ 1) * bufw;
+    switch (R) {
+      case 2: mixed_stage<2, INV>(in_buf, out_buf, SI, b, t, TPL, Ns, A.tw); break;
+      case 3: mixed_stage<3, INV>(in_buf, out_buf, SI, b, t, TPL, Ns, A.tw); break;
+      case 4: mixed_stage<4, INV>(in_buf, out_buf, SI, b, t, TPL, Ns, A.tw); break;
+      case 5: mixed_stage<5, INV>(in_buf, out_buf, SI, b, t, TPL, Ns, A.tw); break;
+      default: mixed_stage<8, INV>(in_buf, out_buf, SI, b, t, TPL, Ns, A.tw); break;
+    }
+    __syncthreads();
+    cur ^= 1;
+    Ns *= R;
+  }
+
+  if (!live) return;
+  const float2* res = sm + cur * bufw;
+  for (int p = t; p < L; p += TPL) {
+    const float2 v = res[SI.at(b, p)];
+    if (!INV) {
+      dst[goff + (int64_t)p * stride + in] = v;
+    } else {
+      if (!((p < half) || (p >= L - half))) continue;
+      if (A.dst_image) {
+        const int n = p < half ? p + half : p - L + half;
+        dst[o * A.Na + n] = cscale(v, (A.scale ? A.s_axis[n] : 1.0f) * slead);
+      } else {
+        dst[goff + (int64_t)p * stride + in] = v;
+      }
+    }
+  }
+}
+
+// 256 threads per CTA: W lines of 256 / W threads (strided axes: W adjacent
+// columns, W | inner), W lowered while the launch would give fewer than two
+// CTAs per SM.
+template <bool STRIDED, bool INV>
+cudaError_t launch_mixed(int L, const FftArgs& A, int nb, cudaStream_t st) {
+  const MixedRadix mr = mixed_radix(L);
+  if (mr.nst < 0) return cudaErrorInvalidValue;
+  int W;
+  int64_t blocks;
+  if (STRIDED) {
+    W = 8;
+    while (W > 1 && (A.inner % W != 0 || A.nouter * (A.inner / W) * nb < kTargetBlocks ||
+                     2 * MixedMap<STRIDED>::words(W, L) * sizeof(float2) > 160 * 1024))
+      W >>= 1;
+    blocks = A.nouter * (A.inner / W);
+  } else {
+    const int tpl = L >= 512 ? 128 : (L >= 128 ? 64 : 32);
+    W = 256 / tpl;
+    while (W > 1 && (A.nouter + W - 1) / W * nb < kTargetBlocks) W >>= 1;
+    blocks = (A.nouter + W - 1) / W;
+  }
+  const int threads = STRIDED ? 256 : W * (L >= 512 ? 128 : (L >= 128 ? 64 : 32));
+  const size_t smem = 2 * MixedMap<STRIDED>::words(W, L) * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_fft_mixed<STRIDED, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  if (blocks == 0) return cudaSuccess;
+  k_fft_mixed<STRIDED, INV><<<dim3((unsigned)blocks, (unsigned)nb), threads, smem, st>>>(A, W, mr);
+  return cudaGetLastError();
+}
+
 template <bool STRIDED, bool INV>
 cudaError_t launch_any(int L, const FftArgs& A, int nb, cudaStream_t st) {
   switch (L) {
@@ -345,7 +577,7 @@ cudaError_t launch_any(int L, const FftArgs& A, int nb, cudaStream_t st) {
     case 256: return launch_L<256, STRIDED, INV>(A, nb, st);
     case 512: return launch_L<512, STRIDED, INV>(A, nb, st);
     case 1024: return launch_L<1024, STRIDED, INV>(A, nb, st);
-    default: return cudaErrorInvalidValue;
+    default: return launch_mixed<STRIDED, INV>(L, A, nb, st);
   }
 }
 

@@ -36,7 +36,7 @@ k_traj_grad(const float2* __restrict__ grid, const float2* __restrict__ gy, floa
   for (int a = 0; a < D; ++a) part[a] = make_float2(0.f, 0.f);
   if (active) {
     const int kl = P.kf[(int64_t)(D - 1) * P.M + i];
-    const int gl = (kl + l) & (g.K[D - 1] - 1);
+    const int gl = wrapk(kl + l, g.K[D - 1]);
     const int64_t cl_idx = P.coef_off[D - 1] + (int64_t)l * P.M + i;
     const float2 cl = P.coef[cl_idx];
     const float2 dcl = Dv.dcoef[cl_idx];
@@ -48,7 +48,7 @@ k_traj_grad(const float2* __restrict__ grid, const float2* __restrict__ gy, floa
       float2 acc_c = make_float2(0.f, 0.f), acc_d = make_float2(0.f, 0.f);
       for (int j0 = 0; j0 < J0; ++j0) {
         const int64_t ci = P.coef_off[0] + (int64_t)j0 * P.M + i;
-        const float2 v = __ldg(&grid[((k0 + j0) & (g.K[0] - 1)) * (int)g.Kstride[0] + gl]);
+        const float2 v = __ldg(&grid[wrapk(k0 + j0, g.K[0]) * (int)g.Kstride[0] + gl]);
         acc_c = cadd(acc_c, cmul(P.coef[ci], v));
         acc_d = cadd(acc_d, cmul(Dv.dcoef[ci], v));
       }
@@ -62,11 +62,11 @@ k_traj_grad(const float2* __restrict__ grid, const float2* __restrict__ gy, floa
       for (int j0 = 0; j0 < J0; ++j0) {
         const int64_t c0i = P.coef_off[0] + (int64_t)j0 * P.M + i;
         const float2 c0 = P.coef[c0i], dc0 = Dv.dcoef[c0i];
-        const float2* plane = grid + ((k0 + j0) & (g.K[0] - 1)) * (int)g.Kstride[0];
+        const float2* plane = grid + wrapk(k0 + j0, g.K[0]) * (int)g.Kstride[0];
         float2 s_c = make_float2(0.f, 0.f), s_d = make_float2(0.f, 0.f);
         for (int j1 = 0; j1 < J1; ++j1) {
           const int64_t c1i = P.coef_off[1] + (int64_t)j1 * P.M + i;
-          const float2 v = __ldg(&plane[((k1 + j1) & (g.K[1] - 1)) * (int)g.Kstride[1] + gl]);
+          const float2 v = __ldg(&plane[wrapk(k1 + j1, g.K[1]) * (int)g.Kstride[1] + gl]);
           s_c = cadd(s_c, cmul(P.coef[c1i], v));
           s_d = cadd(s_d, cmul(Dv.dcoef[c1i], v));
         }

@@ -38,7 +38,11 @@ int run_graphed_impl(nufft_plan_t* p, int kind, const void* a, const void* b, in
     }
     if (slot->state == 2 && slot->exec) cudaGraphExecDestroy(slot->exec);
     *slot = GraphEntry{kind, a, b, extra, p->stream, 1, nullptr, ++p->graph_clock};
-    return fn(ctx);
+    const int rc = fn(ctx);
+    // a failed first call (e.g. a work-space allocation) does not count: the
+    // next call runs eagerly again instead of allocating inside a capture
+    if (rc != NUFFT_OK) *slot = GraphEntry{};
+    return rc;
   }
   e->last_use = ++p->graph_clock;
   if (e->state == 3) return fn(ctx);

@@ -27,13 +27,11 @@ constexpr int kChunkPoints[4] = {0, 1024, 256, 2048};
 struct Geom {
   int d;
   int N[kMaxDim];      // image size
-  int K[kMaxDim];      // grid size (power of two)
+  int K[kMaxDim];      // grid size (even; prime factors 2, 3, 5)
   int J[kMaxDim];      // neighbours
-  int T[kMaxDim];      // tile edge
+  int T[kMaxDim];      // tile edge: a divisor of K with T >= J - 1
   int nb[kMaxDim];     // tiles per dimension = K / T
   int P[kMaxDim];      // padded tile edge = T + J - 1
-  int lT[kMaxDim];     // log2 T
-  int lnb[kMaxDim];    // log2 nb
   int64_t Kstride[kMaxDim];  // C-order strides of the grid
   int64_t nbins;
   int64_t padded_cells;      // prod P
@@ -46,6 +44,7 @@ struct Points {
   const float2* coef;    // dim i starts at coef + coef_off[i]; layout [J_i][M]
   int64_t coef_off[kMaxDim];
   const int32_t* perm;   // sorted position -> trajectory index
+  const uint32_t* cmax;  // [d] largest |coefficient| of each dimension (float bits)
 };
 
 struct Chunk {
@@ -78,6 +77,7 @@ struct nufft_plan {
   int64_t Nprod;
   int64_t Kprod;
   cudaStream_t stream;
+  int device;               // CUDA device current when the plan was made (its memory lives there)
 
   // plan-owned device memory
   float* s;                 // scaling, dim i at s + s_off[i]
@@ -123,6 +123,7 @@ struct nufft_plan {
   uint32_t* sort_hist;      // [256][ceil(M / sort tile)]
   int32_t* perm2;           // [M]
   int* flags;               // [2]: om invalid, G singular
+  uint32_t* cmax;           // [kMaxDim] largest |coefficient| per dimension (float bits), for the gridding scale
   int64_t chunk_cap;
   uint64_t generation;      // bumped whenever recorded graphs may be stale (drop_graphs)
 
@@ -160,6 +161,16 @@ int cuda_check(nufft_plan_t* p, cudaError_t e, const char* what);
     cudaError_t _e = (call);                                      \
     if (_e != cudaSuccess) return ::nufft::cuda_check((p), _e, #call); \
   } while (0)
+
+// ------------------------------------------------------------------ device memory (memory.cu)
+// All library-owned device buffers go through these (a test hook can make an
+// allocation fail; the bytes held are counted).
+cudaError_t dev_malloc_bytes(void** ptr, size_t bytes);
+cudaError_t dev_free(void* ptr);
+template <class T>
+inline cudaError_t dev_malloc(T** ptr, size_t bytes) {
+  return dev_malloc_bytes(reinterpret_cast<void**>(ptr), bytes);
+}
 
 // ------------------------------------------------------------------ launchers
 // FFT passes (fft.cu).  Forward: grid = F pad(S x).  Inverse: x = S crop(F^H grid).
@@ -226,6 +237,9 @@ int ensure_coef_derivatives(nufft_plan_t* p);
 }  // namespace nufft
 
 // ------------------------------------------------------------------ complex helpers
+// Grid index k0 + j wrapped into [0, K), for k0 in [0, K) and 0 <= j < K.
+__host__ __device__ __forceinline__ int wrapk(int v, int K) { return v >= K ? v - K : v; }
+
 __host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }

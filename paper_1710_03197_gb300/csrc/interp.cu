@@ -50,7 +50,7 @@ k_interp(const float2* __restrict__ grid_b, float2* __restrict__ y_b, const Poin
     const int J1 = JF > 0 ? JF : (D > 1 ? g.J[1] : 1);
     const int kl = P.kf[(int64_t)(D - 1) * P.M + i];
     const int Klast = g.K[D - 1];
-    const int gl = (kl + l) & (Klast - 1);
+    const int gl = wrapk(kl + l, Klast);
     const float2 cl = P.coef[P.coef_off[D - 1] + (int64_t)l * P.M + i];
     if (D == 1) {
       part = cmul(cl, __ldg(&grid[gl]));
@@ -61,7 +61,7 @@ k_interp(const float2* __restrict__ grid_b, float2* __restrict__ y_b, const Poin
       for (int j0 = 0; j0 < (JF > 0 ? JF : kMaxJ); ++j0) {
         if (JF == 0 && j0 >= J0) break;
         const float2 c0 = P.coef[P.coef_off[0] + (int64_t)j0 * P.M + i];
-        const int row = ((k0 + j0) & (g.K[0] - 1)) * (int)g.Kstride[0];
+        const int row = wrapk(k0 + j0, g.K[0]) * (int)g.Kstride[0];
         acc = cadd(acc, cmul(c0, __ldg(&grid[row + gl])));
       }
       part = cmul(cl, acc);
@@ -79,13 +79,13 @@ k_interp(const float2* __restrict__ grid_b, float2* __restrict__ y_b, const Poin
 #pragma unroll
       for (int j1 = 0; j1 < (JF > 0 ? JF : kMaxJ); ++j1) {
         if (JF == 0 && j1 >= J1) break;
-        rowoff[j1] = ((k1 + j1) & (g.K[1] - 1)) * (int)g.Kstride[1] + gl;
+        rowoff[j1] = wrapk(k1 + j1, g.K[1]) * (int)g.Kstride[1] + gl;
       }
       float2 acc = make_float2(0.f, 0.f);
 #pragma unroll 1
       for (int j0 = 0; j0 < J0; ++j0) {
         const float2 c0 = P.coef[P.coef_off[0] + (int64_t)j0 * P.M + i];
-        const float2* plane = grid + ((k0 + j0) & (g.K[0] - 1)) * (int)g.Kstride[0];
+        const float2* plane = grid + wrapk(k0 + j0, g.K[0]) * (int)g.Kstride[0];
         float2 acc1 = make_float2(0.f, 0.f);
 #pragma unroll
         for (int j1 = 0; j1 < (JF > 0 ? JF : kMaxJ); ++j1) {
@@ -109,12 +109,107 @@ k_interp(const float2* __restrict__ grid_b, float2* __restrict__ y_b, const Poin
 }
 
 // ---------------------------------------------------------------- gridding, per chunk
-// The shared tile is held as two planes (real parts, then imaginary parts) so
-// that the J_last lanes of a point hit J_last consecutive banks per atomic.
+// Deterministic accumulation.  The points of a chunk add into a shared copy
+// of the padded tile in fixed point: every contribution is scaled by a power
+// of two S chosen per chunk (and batch element), rounded to an integer and
+// added with a 32-bit integer atomic.  Integer addition is exact and
+// associative, so the padded tile does not depend on the order in which the
+// warps' atomics land, and two runs give bit-identical grids.  S comes from
+// a bound on every cell's sum of magnitudes,
+//   B = cbound * sum over the chunk's points of (|Re y| + |Im y|),
+// cbound = prod_d max |c_d| (a point adds to a cell at most once), taken in a
+// fixed order, so S is the same on every run too:
+//   1D, 2D (chunks of <= 1024, <= 256 points): one int32 word per component,
+//     sums below 2^30 (S = 2^(30 - E), B < 2^E); a contribution's rounding
+//     error is at most 2^-31 B;
+//   3D (chunks of <= 2048 points): 2^34 of range in three words per cell: the
+//     part above 2^20 of both components packed as two 16-bit fields of one
+//     word (|sum| <= 2^14 + 1024 each), and the remainders below 2^20 in one
+//     word each (|sum| <= 2048 * 2^19); rounding error at most 2^-35 B.
+// A chunk whose bound is not finite (an Inf or NaN sample) writes NaN.
+template <int D>
+struct Fix {
+  static constexpr int kBits = D == 3 ? 34 : 30;   // range of a cell's sum, log2
+  static constexpr int kWords = D == 3 ? 3 : 2;    // int32 words per cell
+};
+
+// Sum of v over the CTA in a fixed order (shuffle tree, then warps in order);
+// every thread gets the sum.  red: 32 floats of shared scratch.
+__device__ __forceinline__ float block_sum_fixed(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float t = 0.f;
+  for (int w = 0; w < nw; ++w) t += red[w];
+  __syncthreads();   // red free for reuse
+  return t;
+}
+
+struct ChunkScale {
+  float S, inv;   // power-of-two scale and its inverse
+  bool finite;
+};
+
+template <int D>
+__device__ __forceinline__ ChunkScale chunk_scale(float ysum, const uint32_t* cmax) {
+  float cb = 1.f;
+#pragma unroll
+  for (int a = 0; a < D; ++a) cb *= __uint_as_float(__ldg(&cmax[a]));
+  const float B = ysum * cb;
+  ChunkScale cs;
+  cs.finite = isfinite(B);
+  int E = 0;
+  frexpf(cs.finite ? B : 0.f, &E);                   // B < 2^E
+  E = max(E, Fix<D>::kBits - 126);                   // keep S and 1/S normal floats
+  cs.S = ldexpf(1.f, Fix<D>::kBits - E);
+  cs.inv = ldexpf(1.f, E - Fix<D>::kBits);
+  return cs;
+}
+
+// Add one contribution w (already scaled by S) to cell `cell`.
+//   D < 3: acc[0][cell] += rn(Re w), acc[1][cell] += rn(Im w)
+//   D = 3: packed high parts in acc[0], remainders in acc[1], acc[2]
+template <int D>
+__device__ __forceinline__ void fix_add(int* acc, int ncell, int cell, float2 w) {
+  if (D < 3) {
+    atomicAdd(&acc[cell], __float2int_rn(w.x));
+    atomicAdd(&acc[ncell + cell], __float2int_rn(w.y));
+  } else {
+    // x + 1.5 * 2^23 rounds x to an integer when |x| < 2^22, and the float's
+    // bits minus those of 1.5 * 2^23 are that integer.
+    const float magic = 12582912.0f;
+    const float hr = fmaf(w.x, 0x1p-20f, magic), hi_ = fmaf(w.y, 0x1p-20f, magic);
+    const float lr = fmaf(-(hr - magic), 0x1p20f, w.x) + magic;   // remainder (exact), rounded
+    const float li = fmaf(-(hi_ - magic), 0x1p20f, w.y) + magic;
+    const int hre = __float_as_int(hr) - 0x4B400000, him = __float_as_int(hi_) - 0x4B400000;
+    atomicAdd(&acc[cell], him * 65536 + hre);
+    atomicAdd(&acc[ncell + cell], __float_as_int(lr) - 0x4B400000);
+    atomicAdd(&acc[2 * ncell + cell], __float_as_int(li) - 0x4B400000);
+  }
+}
+
+// Value of cell c of the fixed-point tile, unscaled.
+template <int D>
+__device__ __forceinline__ float2 fix_value(const int* acc, int ncell, int c, const ChunkScale& cs) {
+  if (!cs.finite) return make_float2(__int_as_float(0x7fffffff), __int_as_float(0x7fffffff));
+  if (D < 3) return make_float2((float)acc[c] * cs.inv, (float)acc[ncell + c] * cs.inv);
+  const int w = acc[c];
+  const int hre = (int)(short)(w & 0xffff);   // low field, sign-extended
+  const int him = (w - hre) / 65536;
+  const long long re = (long long)hre * 1048576 + acc[ncell + c];
+  const long long im = (long long)him * 1048576 + acc[2 * ncell + c];
+  return make_float2((float)re * cs.inv, (float)im * cs.inv);
+}
+
+// The accumulator words are held as planes (word k of every cell, then word
+// k + 1, ...) so that the J_last lanes of a point hit J_last consecutive banks
+// per atomic.
 template <int D, int JF>
 struct GridChunkCfg {
   static constexpr int kThreads = D == 3 ? 512 : 256;
-  static constexpr int kMinBlocks = D == 3 ? (JF == 6 ? 3 : 2) : 4;
+  static constexpr int kMinBlocks = D == 3 ? 2 : 4;
 };
 
 // TF > 0: every tile edge is TF and every J is JF, so the padded-tile pitches
@@ -126,23 +221,29 @@ k_gridding_chunk(const float2* __restrict__ y_b, float2* __restrict__ tiles_b, c
                  const Points P, const Geom g, int64_t ybs, int64_t tbs) {
   static_assert(TF == 0 || JF > 0, "a fixed tile needs a fixed J");
   constexpr int PF = TF > 0 ? TF + JF - 1 : 0;   // padded edge when fixed
-  extern __shared__ float sm[];
+  extern __shared__ int acc[];
+  __shared__ float red[32];
   const float2* __restrict__ y = y_b + (int64_t)blockIdx.y * ybs;
   float2* __restrict__ tiles = tiles_b + (int64_t)blockIdx.y * tbs;
   const int ncell = TF > 0 ? (D == 1 ? PF : (D == 2 ? PF * PF : PF * PF * PF)) : (int)g.padded_cells;
-  float* sre = sm;
-  float* sim = sm + ncell;
   const Chunk ch = chunks[blockIdx.x];
-  for (int c = threadIdx.x; c < 2 * ncell; c += blockDim.x) sm[c] = 0.f;
-  __syncthreads();
+  for (int c = threadIdx.x; c < Fix<D>::kWords * ncell; c += blockDim.x) acc[c] = 0;
+
+  // the chunk's scale (the sum also orders the zeroing above before the atomics)
+  float part = 0.f;
+  for (int q = threadIdx.x; q < ch.count; q += blockDim.x) {
+    const float2 v = __ldg(&y[P.perm[(int64_t)ch.start + q]]);
+    part += fabsf(v.x) + fabsf(v.y);
+  }
+  const ChunkScale cs = chunk_scale<D>(block_sum_fixed(part, red), P.cmax);
 
   // tile origin of this chunk's bin
   int org[kMaxDim];
   {
     int rem = ch.bin;
     for (int a = D - 1; a >= 0; --a) {
-      org[a] = (rem & (g.nb[a] - 1)) << g.lT[a];
-      rem >>= g.lnb[a];
+      org[a] = (rem % g.nb[a]) * g.T[a];
+      rem /= g.nb[a];
     }
   }
   const int G = JF > 0 ? JF : g.J[D - 1];
@@ -158,7 +259,7 @@ k_gridding_chunk(const float2* __restrict__ y_b, float2* __restrict__ tiles_b, c
   // Consecutive points of the chunk share a warp instruction: the plan orders
   // each chunk so that every aligned group of per_warp points covers disjoint
   // shared-memory bank windows (see the bank-order kernel in plan.cu).
-  if (sub < per_warp) {
+  if (sub < per_warp && cs.finite) {
     const int stepq = nwarps * per_warp;
     int q = warp * per_warp + sub;
     // 1D/2D: the dependent load (sample through the permutation) runs one
@@ -175,12 +276,12 @@ k_gridding_chunk(const float2* __restrict__ y_b, float2* __restrict__ tiles_b, c
       } else {
         yv = __ldg(&y[P.perm[i]]);
       }
+      yv = cscale(yv, cs.S);
       const int ll = P.kf[(int64_t)(D - 1) * P.M + i] - org[D - 1] + l;
       const float2 cl = P.coef[P.coef_off[D - 1] + (int64_t)l * P.M + i];
       const float2 yl = cmulc(cl, yv);  // conj(c_last) * y
       if (D == 1) {
-        atomicAdd(&sre[ll], yl.x);
-        atomicAdd(&sim[ll], yl.y);
+        fix_add<D>(acc, ncell, ll, yl);
       } else if (D == 2) {
         const int l0 = P.kf[i] - org[0];
         const int J0 = JF > 0 ? JF : g.J[0];
@@ -188,10 +289,7 @@ k_gridding_chunk(const float2* __restrict__ y_b, float2* __restrict__ tiles_b, c
         for (int j0 = 0; j0 < (JF > 0 ? JF : kMaxJ); ++j0) {
           if (JF == 0 && j0 >= J0) break;
           const float2 c0 = P.coef[P.coef_off[0] + (int64_t)j0 * P.M + i];
-          const float2 w = cmulc(c0, yl);
-          const int cell = (l0 + j0) * P1 + ll;
-          atomicAdd(&sre[cell], w.x);
-          atomicAdd(&sim[cell], w.y);
+          fix_add<D>(acc, ncell, (l0 + j0) * P1 + ll, cmulc(c0, yl));
         }
       } else {
         const int l0 = P.kf[i] - org[0];
@@ -213,10 +311,7 @@ k_gridding_chunk(const float2* __restrict__ y_b, float2* __restrict__ tiles_b, c
 #pragma unroll
           for (int j1 = 0; j1 < (JF > 0 ? JF : kMaxJ); ++j1) {
             if (JF == 0 && j1 >= J1) break;
-            const float2 w = cmulc(c1v[j1], w0);
-            const int cell = rowbase + j1 * P2;
-            atomicAdd(&sre[cell], w.x);
-            atomicAdd(&sim[cell], w.y);
+            fix_add<D>(acc, ncell, rowbase + j1 * P2, cmulc(c1v[j1], w0));
           }
         }
       }
@@ -224,7 +319,7 @@ k_gridding_chunk(const float2* __restrict__ y_b, float2* __restrict__ tiles_b, c
   }
   __syncthreads();
   float2* out = tiles + (int64_t)blockIdx.x * g.padded_cells;
-  for (int c = threadIdx.x; c < ncell; c += blockDim.x) out[c] = make_float2(sre[c], sim[c]);
+  for (int c = threadIdx.x; c < ncell; c += blockDim.x) out[c] = fix_value<D>(acc, ncell, c, cs);
 }
 
 // ---------------------------------------------------------------- gridding, tile reduction
@@ -252,8 +347,8 @@ __device__ __forceinline__ void reduce_tile(const float2* __restrict__ tiles, co
     int rem = bin;
 #pragma unroll
     for (int a = D - 1; a >= 0; --a) {
-      bc[a] = rem & (g.nb[a] - 1);
-      rem >>= g.lnb[a];
+      bc[a] = rem % g.nb[a];
+      rem /= g.nb[a];
     }
   }
   const int P1 = D > 1 ? g.P[1] : 1, P2 = D > 2 ? g.P[2] : 1;
@@ -262,7 +357,7 @@ __device__ __forceinline__ void reduce_tile(const float2* __restrict__ tiles, co
     int src = 0, delta = 0;
     for (int a = 0; a < D; ++a) {
       const int ea = (e >> (D - 1 - a)) & 1;
-      src = (src << g.lnb[a]) | ((bc[a] - ea) & (g.nb[a] - 1));
+      src = src * g.nb[a] + (bc[a] - ea + g.nb[a]) % g.nb[a];
       const int pstride = a == D - 1 ? 1 : (a == D - 2 ? g.P[D - 1] : P1 * P2);
       delta += ea * g.T[a] * pstride;
     }
@@ -296,12 +391,12 @@ __device__ __forceinline__ void reduce_tile(const float2* __restrict__ tiles, co
     if (D == 1) {
       lc[0] = c;
     } else if (D == 2) {
-      lc[1] = c & (T1 - 1);
-      lc[0] = c >> g.lT[1];
+      lc[1] = c % T1;
+      lc[0] = c / T1;
     } else {
-      lc[2] = c & (T2 - 1);
-      lc[1] = (c >> g.lT[2]) & (T1 - 1);
-      lc[0] = c >> (g.lT[2] + g.lT[1]);
+      lc[2] = c % T2;
+      lc[1] = (c / T2) % T1;
+      lc[0] = c / (T2 * T1);
     }
     loc0[k] = D == 1 ? lc[0] : (D == 2 ? lc[0] * P1 + lc[1] : (lc[0] * P1 + lc[1]) * P2 + lc[2]);
     unsigned m = 0;
@@ -316,7 +411,7 @@ __device__ __forceinline__ void reduce_tile(const float2* __restrict__ tiles, co
     emask[k] = (cbase + tg + k * gsize < cend) ? m : 0u;
     int off = 0;
 #pragma unroll
-    for (int a = 0; a < D; ++a) off += ((bc[a] << g.lT[a]) + lc[a]) * (int)g.Kstride[a];
+    for (int a = 0; a < D; ++a) off += (bc[a] * g.T[a] + lc[a]) * (int)g.Kstride[a];
     goff[k] = off;
   }
   const int64_t pc = g.padded_cells;
@@ -396,38 +491,38 @@ k_gridding_reduce(const float2* __restrict__ tiles_b, const int32_t* __restrict_
 // are first copied into shared memory by all threads at once, so the CTA waits
 // for two dependent global round trips (the permutation, then the samples)
 // instead of one per pass of its warps over the chunk.  The accumulation then
-// follows the same lane layout and bank order as k_gridding_chunk.
-// Shared memory: the split-plane tile, then c0[J0][cap] (row by row: the lanes
-// of a point read one value), c1[cap][J1] (point by point: the J1 lanes of a
-// point read consecutive words, so a warp's 64-bit reads of five points hit
-// distinct bank pairs), y[cap], k[2][cap] (first neighbours relative to the
-// tile origin), cap = chunk size.
+// follows the same lane layout, bank order and fixed-point words as
+// k_gridding_chunk.
+// Shared memory: the two accumulator planes, then c0[J0][cap] (row by row:
+// the lanes of a point read one value), c1[cap][J1] (point by point: the J1
+// lanes of a point read consecutive words, so a warp's 64-bit reads of five
+// points hit distinct bank pairs), y[cap], k[2][cap] (first neighbours
+// relative to the tile origin), cap = chunk size.
 // FUSED (V^H V, the normal operator's grid part): y_b is the oversampled
-// spectrum instead of the samples, and each point's y is gathered from it in
-// the scatter's own lane layout (the interpolation's arithmetic and summation
-// order) right before it is scattered, so the samples never leave the CTA and
-// the coefficients are read once for both directions.
+// spectrum instead of the samples; each point's y is first gathered from it
+// into shared memory (the interpolation's arithmetic and summation order, in
+// the scatter's lane layout), so the samples never leave the CTA and the
+// coefficients are read once for both directions.
 template <int JF, bool FUSED>
 __global__ void __launch_bounds__(256, 4)
 k_gridding_chunk_staged(const float2* __restrict__ y_b, float2* __restrict__ tiles_b,
                         const Chunk* __restrict__ chunks, const Points P, const Geom g, int64_t ybs, int64_t tbs) {
   constexpr int cap = kChunkPoints[2];
-  extern __shared__ float sm[];
+  extern __shared__ int acc[];
+  __shared__ float red[32];
   const float2* __restrict__ y = y_b + (int64_t)blockIdx.y * ybs;
   float2* __restrict__ tiles = tiles_b + (int64_t)blockIdx.y * tbs;
   const int ncell = (int)g.padded_cells;
-  float* sre = sm;
-  float* sim = sm + ncell;
   const int J0 = JF > 0 ? JF : g.J[0];
   const int J1 = JF > 0 ? JF : g.J[1];
-  float2* s_c = reinterpret_cast<float2*>(sm + 2 * ncell);   // 8-byte aligned: 2 * ncell floats
+  float2* s_c = reinterpret_cast<float2*>(acc + 2 * ncell);   // 8-byte aligned: 2 * ncell words
   float2* s_y = s_c + (J0 + J1) * cap;
   int* s_k = reinterpret_cast<int*>(s_y + cap);
   const Chunk ch = chunks[blockIdx.x];
-  const int org0 = ((ch.bin >> g.lnb[1]) & (g.nb[0] - 1)) << g.lT[0];
-  const int org1 = (ch.bin & (g.nb[1] - 1)) << g.lT[1];
+  const int org0 = ((ch.bin / g.nb[1]) % g.nb[0]) * g.T[0];
+  const int org1 = (ch.bin % g.nb[1]) * g.T[1];
 
-  for (int c = threadIdx.x; c < 2 * ncell; c += blockDim.x) sm[c] = 0.f;
+  for (int c = threadIdx.x; c < 2 * ncell; c += blockDim.x) acc[c] = 0;
   static_assert(cap == 256, "one thread per staged point");
   const int qs = threadIdx.x;           // the point this thread stages
   int pm = 0;
@@ -462,24 +557,21 @@ k_gridding_chunk_staged(const float2* __restrict__ y_b, float2* __restrict__ til
   if (FUSED) {
     // warp-uniform rounds of per_warp points: the lane-group sum is a
     // full-warp shuffle
-    const int K0m = g.K[0] - 1, K1m = g.K[1] - 1;
     const int ks0 = (int)g.Kstride[0];
     for (int qb = warp * per_warp; qb < ch.count; qb += nwarps * per_warp) {
       const int q = qb + sub;
       const bool act = (sub < per_warp) && (q < ch.count);
       float2 part = make_float2(0.f, 0.f);
-      float2 cl = make_float2(0.f, 0.f);
       if (act) {
-        const int gl = (s_k[cap + q] + org1 + l) & K1m;
+        const int gl = wrapk(s_k[cap + q] + org1 + l, g.K[1]);
         const int k0 = s_k[q] + org0;
-        float2 acc = make_float2(0.f, 0.f);
+        float2 a = make_float2(0.f, 0.f);
 #pragma unroll
         for (int j0 = 0; j0 < (JF > 0 ? JF : kMaxJ); ++j0) {
           if (JF == 0 && j0 >= J0) break;
-          acc = cadd(acc, cmul(s_c[j0 * cap + q], __ldg(&y[((k0 + j0) & K0m) * ks0 + gl])));
+          a = cadd(a, cmul(s_c[j0 * cap + q], __ldg(&y[wrapk(k0 + j0, g.K[0]) * ks0 + gl])));
         }
-        cl = s_c[J0 * cap + q * J1 + l];
-        part = cmul(cl, acc);
+        part = cmul(s_c[J0 * cap + q * J1 + l], a);
       }
       const int base = sub * G;
       float2 yv = make_float2(0.f, 0.f);
@@ -488,39 +580,29 @@ k_gridding_chunk_staged(const float2* __restrict__ y_b, float2* __restrict__ til
         yv.x += __shfl_sync(0xffffffffu, part.x, src);
         yv.y += __shfl_sync(0xffffffffu, part.y, src);
       }
-      if (act) {
-        const float2 yl = cmulc(cl, yv);   // conj(c_last) * y
-        const int ll = s_k[cap + q] + l;
-        const int l0 = s_k[q];
-#pragma unroll
-        for (int j0 = 0; j0 < (JF > 0 ? JF : kMaxJ); ++j0) {
-          if (JF == 0 && j0 >= J0) break;
-          const float2 w = cmulc(s_c[j0 * cap + q], yl);
-          const int cell = (l0 + j0) * P1 + ll;
-          atomicAdd(&sre[cell], w.x);
-          atomicAdd(&sim[cell], w.y);
-        }
-      }
+      if (act && l == 0) s_y[q] = yv;
     }
-  } else if (sub < per_warp) {
+    __syncthreads();
+  }
+  // the chunk's scale (also orders the zeroing and staging before the atomics)
+  float mag = 0.f;
+  if (qs < ch.count) mag = fabsf(s_y[qs].x) + fabsf(s_y[qs].y);
+  const ChunkScale cs = chunk_scale<2>(block_sum_fixed(mag, red), P.cmax);
+  if (sub < per_warp && cs.finite) {
     for (int q = warp * per_warp + sub; q < ch.count; q += nwarps * per_warp) {
-      const float2 yl = cmulc(s_c[J0 * cap + q * J1 + l], s_y[q]);   // conj(c_last) * y
+      const float2 yl = cmulc(s_c[J0 * cap + q * J1 + l], cscale(s_y[q], cs.S));   // conj(c_last) * y * S
       const int ll = s_k[cap + q] + l;
       const int l0 = s_k[q];
 #pragma unroll
       for (int j0 = 0; j0 < (JF > 0 ? JF : kMaxJ); ++j0) {
         if (JF == 0 && j0 >= J0) break;
-        const float2 w = cmulc(s_c[j0 * cap + q], yl);
-        const int cell = (l0 + j0) * P1 + ll;
-        atomicAdd(&sre[cell], w.x);
-        atomicAdd(&sim[cell], w.y);
+        fix_add<2>(acc, ncell, (l0 + j0) * P1 + ll, cmulc(s_c[j0 * cap + q], yl));
       }
     }
   }
   __syncthreads();
   float2* out = tiles + (int64_t)blockIdx.x * g.padded_cells;
-  for (int c = threadIdx.x; c < ncell; c += blockDim.x) out[c] = make_float2(sre[c], sim[c]);
-
+  for (int c = threadIdx.x; c < ncell; c += blockDim.x) out[c] = fix_value<2>(acc, ncell, c, cs);
 }
 
 // The reduction gives every thread 4 cells of the tile; small tiles get up to 4
@@ -534,7 +616,7 @@ cudaError_t launch_reduce(const nufft_plan_t* p, const float2* tiles, float2* gr
   // CTA of 64 registers filled an SM: 1 -> 2 -> 4 -> 8 slices measured 0.909,
   // 0.887, 0.875, 0.864 ms for the kooshball's gridding; 16 no better)
   const int slices = (D == 3 && cells >= 4096) ? 8 : 1;
-  const int gsize = std::max(32, std::min(1024, cells / 4 / slices));
+  const int gsize = std::max(32, std::min(1024, (cells / slices + 4 * 32 - 1) / (4 * 32) * 32));
   if ((int64_t)gsize * 4 * slices < cells) return cudaErrorInvalidValue;
   // groups splitting the chunk list; a batch (mostly sparse tiles, many CTAs)
   // runs one group per CTA so that more tiles are in flight per SM
@@ -576,7 +658,7 @@ cudaError_t launch_chunks(const nufft_plan_t* p, const float2* y, float2* tiles,
   cudaError_t e;
   if constexpr (D == 2) {
     const int sj = p->g.J[0] + p->g.J[1];
-    const size_t smem = (size_t)p->g.padded_cells * sizeof(float2) +
+    const size_t smem = (size_t)p->g.padded_cells * Fix<2>::kWords * sizeof(int) +
                         (size_t)kChunkPoints[2] * ((size_t)sj * sizeof(float2) + sizeof(float2) + 2 * sizeof(int));
     auto kern = j6 ? k_gridding_chunk_staged<6, FUSED> : k_gridding_chunk_staged<0, FUSED>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -584,7 +666,7 @@ cudaError_t launch_chunks(const nufft_plan_t* p, const float2* y, float2* tiles,
     kern<<<gd, kChunkPoints[2], smem, p->stream>>>(y, tiles, p->chunks, P, p->g, ybs, tbs);
   } else {
     static_assert(!FUSED, "the fused V^H V pass is 2D only");
-    const size_t smem = (size_t)p->g.padded_cells * sizeof(float2);
+    const size_t smem = (size_t)p->g.padded_cells * Fix<D>::kWords * sizeof(int);
     constexpr int NT = GridChunkCfg<D, 6>::kThreads;
     bool t16 = D == 3;
     for (int a = 0; a < D; ++a) t16 = t16 && p->g.T[a] == 16;
@@ -615,9 +697,11 @@ constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
 float2* g_static_ptr[kMaxDevices];   // device address of g_static_tiles, per device
 
+// Device address of the static array on the plan's device, which the caller
+// has made current.  Looked up once per device (cudaGetSymbolAddress) and
+// cached; the host-side name g_static_tiles is not a device address.
 int static_tiles_address(nufft_plan_t* p, float2** out) {
-  int dev = -1;
-  NUFFT_CUDA_TRY(p, cudaGetDevice(&dev));
+  const int dev = p->device;
   if (dev < 0 || dev >= kMaxDevices) return set_error(p, NUFFT_EINVAL, "device ordinal %d out of range", dev);
   std::lock_guard<std::mutex> lock(g_static_mu);
   if (!g_static_ptr[dev]) {
@@ -628,6 +712,22 @@ int static_tiles_address(nufft_plan_t* p, float2** out) {
   *out = g_static_ptr[dev];
   return NUFFT_OK;
 }
+
+// Makes the plan's device current for the call and puts the caller's back.
+struct DeviceScope {
+  int prev = -1;
+  bool switched = false;
+  ~DeviceScope() {
+    if (switched) cudaSetDevice(prev);
+  }
+  cudaError_t enter(int dev) {
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e != cudaSuccess || prev == dev) return e;
+    e = cudaSetDevice(dev);
+    switched = e == cudaSuccess;
+    return e;
+  }
+};
 
 template <int D>
 cudaError_t gridding_static_d(const nufft_plan_t* p, const float2* y, float2* grid, float2* tiles) {
@@ -684,6 +784,8 @@ extern "C" int nufft_gridding_static(nufft_plan_t* p, const float* y_dev, float*
     return set_error(p, NUFFT_EINVAL,
                      "gridding needs %lld bytes of partial tiles, more than the %lld-byte static scratch; "
                      "use nufft_gridding", (long long)need, (long long)kStaticTileBytes);
+  DeviceScope scope;   // the kernels run on the plan's stream, so on the plan's device
+  NUFFT_CUDA_TRY(p, scope.enter(p->device));
   float2* tiles = nullptr;
   const int rc = static_tiles_address(p, &tiles);
   if (rc != NUFFT_OK) return rc;

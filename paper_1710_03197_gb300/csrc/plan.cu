@@ -49,6 +49,7 @@ Points points_view(const nufft_plan_t* p) {
   P.coef = p->coef;
   for (int a = 0; a < kMaxDim; ++a) P.coef_off[a] = p->coef_off[a];
   P.perm = p->perm;
+  P.cmax = p->cmax;
   return P;
 }
 
@@ -441,6 +442,24 @@ __global__ void k_coefficients(const float* om, int om_sorted, Geom g, int64_t M
   if (kf_out) kf_out[(int64_t)a * M + i] = wrap_first(k0, K);
 }
 
+// Largest coefficient magnitude of each dimension, as float bits (non-negative
+// floats order like their bit patterns), for the gridding's fixed-point scale.
+__global__ void k_coef_max(const float2* coef, int64_t M, int d, int J0, int J1, int J2, uint32_t* cmax) {
+  const int64_t n0 = (int64_t)J0 * M, n1 = (int64_t)J1 * M, n2 = (int64_t)J2 * M;
+  const int64_t n = n0 + (d > 1 ? n1 : 0) + (d > 2 ? n2 : 0);
+  float m[kMaxDim] = {0.f, 0.f, 0.f};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 c = coef[i];
+    const int a = i < n0 ? 0 : (i < n0 + n1 ? 1 : 2);
+    m[a] = fmaxf(m[a], sqrtf(c.x * c.x + c.y * c.y));
+  }
+  for (int a = 0; a < d; ++a) {
+    float v = m[a];
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&cmax[a], __float_as_uint(v));
+  }
+}
+
 // Order each chunk's points for the gridding kernel.  Lane groups of J_last
 // lanes handle one point each and G = 32 / J_last consecutive points share a
 // warp instruction; point p's atomics for neighbour tap (j_0..j_{d-1}) land on
@@ -532,14 +551,20 @@ k_bank_order(const float* om, Geom g, const Chunk* chunks, int64_t nchunks, cons
     perm_out[(int64_t)ch.start + o] = perm_in[(int64_t)ch.start + s_out[o]];
 }
 
-bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+// K whose prime factors are all 2, 3 or 5 (the radices of the FFT passes).
+bool fft_size_ok(int v) {
+  if (v < 1) return false;
+  for (int f : {2, 3, 5})
+    while (v % f == 0) v /= f;
+  return v == 1;
+}
 
 template <class T>
 cudaError_t dalloc(nufft_plan_t* p, T** ptr, int64_t count) {
   *ptr = nullptr;
   if (count <= 0) return cudaSuccess;
   const size_t bytes = (size_t)count * sizeof(T);
-  cudaError_t e = cudaMalloc((void**)ptr, bytes);
+  cudaError_t e = dev_malloc((void**)ptr, bytes);
   if (e == cudaSuccess) p->device_bytes += (int64_t)bytes;
   return e;
 }
@@ -548,9 +573,9 @@ void free_plan_memory(nufft_plan_t* p) {
   void* bufs[] = {p->s, p->twiddle, p->kf, p->coef, p->perm, p->bin_start, p->chunks, p->bin_chunk,
                   p->tiles, p->grid, p->ytmp, p->x_stage, p->y_stage, p->solver_ws, p->kspace_ws, p->mbuf,
                   p->s64, p->Tinv, p->om_sorted, p->dcoef, p->bgrid, p->btiles, p->bytmp, p->bimg,
-                  p->cheb, p->sort_keys, p->sort_vals, p->sort_hist, p->perm2, p->flags};
+                  p->cheb, p->sort_keys, p->sort_vals, p->sort_hist, p->perm2, p->flags, p->cmax};
   for (void* b : bufs)
-    if (b) cudaFree(b);
+    if (b) dev_free(b);
 }
 
 DimTables dim_tables(const nufft_plan_t* p) {
@@ -646,14 +671,14 @@ int build_points(nufft_plan_t* p, const float* om) {
   if (nch > p->chunk_cap) {   // grow the chunk list and the partial tiles (and the batched ones, lazily)
     drop_graphs(p);
     for (void* b : {(void*)p->chunks, (void*)p->tiles, (void*)p->btiles})
-      if (b) cudaFree(b);
+      if (b) dev_free(b);
     p->device_bytes -= p->chunk_cap * ((int64_t)sizeof(Chunk) + g.padded_cells * (int64_t)sizeof(float2)) +
                        (p->btiles ? (int64_t)p->batch_cap * p->chunk_cap * g.padded_cells * (int64_t)sizeof(float2) : 0);
     p->chunks = nullptr;
     p->tiles = nullptr;
     if (p->btiles) {   // the other batched buffers are re-made with it
       for (float2** b : {&p->bgrid, &p->bytmp, &p->bimg})
-        if (*b) { cudaFree(*b); *b = nullptr; }
+        if (*b) { dev_free(*b); *b = nullptr; }
       p->device_bytes -= (int64_t)p->batch_cap * (p->Kprod + M + p->Nprod) * (int64_t)sizeof(float2);
       p->btiles = nullptr;
       p->batch_cap = 0;
@@ -692,6 +717,10 @@ int build_points(nufft_plan_t* p, const float* om) {
                                                                p->coef_off[2], 0, p->om_sorted,
                                                                p->cheb_ok[0] ? p->cheb : nullptr);
     NUFFT_CUDA_TRY(p, cudaGetLastError());
+    NUFFT_CUDA_TRY(p, cudaMemsetAsync(p->cmax, 0, kMaxDim * sizeof(uint32_t), st));
+    k_coef_max<<<(unsigned)std::min<int64_t>(1024, (M * d + 255) / 256), 256, 0, st>>>(
+        p->coef, M, d, g.J[0], d > 1 ? g.J[1] : 0, d > 2 ? g.J[2] : 0, p->cmax);
+    NUFFT_CUDA_TRY(p, cudaGetLastError());
     if (p->dcoef) {
       k_coefficients<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
           p->om_sorted, 1, g, M, p->perm, p->s64, D, p->Tinv, nullptr, p->dcoef, p->coef_off[0], p->coef_off[1],
@@ -709,6 +738,8 @@ int build_plan(nufft_plan_t* p, const float* om) {
   cudaStream_t st = p->stream;
 
   NUFFT_CUDA_TRY(p, dalloc(p, &p->flags, 2));
+  NUFFT_CUDA_TRY(p, dalloc(p, &p->cmax, kMaxDim));
+  NUFFT_CUDA_TRY(p, cudaMemsetAsync(p->cmax, 0, kMaxDim * sizeof(uint32_t), st));
   NUFFT_CUDA_TRY(p, cudaMemsetAsync(p->flags, 0, 2 * sizeof(int), st));
   int rc = validate_om(p, om);
   if (rc != NUFFT_OK) return rc;
@@ -735,8 +766,8 @@ int build_plan(nufft_plan_t* p, const float* om) {
   if (M > 0) {
     NUFFT_CUDA_TRY(p, dalloc(p, &p->cheb, (int64_t)d * 2 * kMaxJ * kCheb));
     double* err = nullptr;
-    NUFFT_CUDA_TRY(p, cudaMalloc((void**)&err, 2 * kMaxDim * sizeof(double)));
-    struct G5 { void* a; ~G5() { if (a) cudaFree(a); } } g5{err};
+    NUFFT_CUDA_TRY(p, dev_malloc((void**)&err, 2 * kMaxDim * sizeof(double)));
+    struct G5 { void* a; ~G5() { if (a) dev_free(a); } } g5{err};
     k_cheb_fit<<<2 * d, 64, 0, st>>>(D, p->s64, p->Tinv, p->cheb);
     NUFFT_CUDA_TRY(p, cudaGetLastError());
     k_cheb_check<<<2 * d, 64, 0, st>>>(D, p->s64, p->Tinv, p->cheb, err);
@@ -819,18 +850,27 @@ int create_plan(int d, const int* Nd, const int* Kd, const int* Jd, int64_t M, c
   const int base_tile = tile_edge > 0 ? tile_edge : (d == 1 ? 1024 : 16);
   for (int a = 0; a < d; ++a) {
     const int N = Nd[a], K = Kd[a], J = Jd[a];
-    if (!is_pow2(K) || K < kMinK || K > kMaxK)
-      return set_error(nullptr, NUFFT_EINVAL, "K[%d] = %d must be a power of two in [%d, %d]", a, K, kMinK, kMaxK);
+    if ((K & 1) || !fft_size_ok(K) || K < kMinK || K > kMaxK)
+      return set_error(nullptr, NUFFT_EINVAL,
+                       "K[%d] = %d must be even, in [%d, %d], with no prime factor other than 2, 3 and 5", a, K,
+                       kMinK, kMaxK);
     if (N < 2 || (N & 1) || N > K)
       return set_error(nullptr, NUFFT_EINVAL, "N[%d] = %d must be even with 2 <= N <= K = %d", a, N, K);
     if (J < 1 || J > kMaxJ || J > K)
       return set_error(nullptr, NUFFT_EINVAL, "J[%d] = %d must satisfy 1 <= J <= min(16, K)", a, J);
     g.N[a] = N; g.K[a] = K; g.J[a] = J;
-    g.T[a] = std::min(base_tile, K);
-    g.nb[a] = K / g.T[a];
-    g.P[a] = g.T[a] + J - 1;
-    while ((1 << g.lT[a]) < g.T[a]) ++g.lT[a];
-    while ((1 << g.lnb[a]) < g.nb[a]) ++g.lnb[a];
+    // tile edge: the largest divisor of K not above the base edge; if that is
+    // below J - 1 (a point's footprint would reach past the next tile), the
+    // smallest divisor of K from J - 1 up
+    int T = 1;
+    for (int t = std::min(base_tile, K); t >= 1; --t)
+      if (K % t == 0) { T = t; break; }
+    if (T < J - 1)
+      for (int t = J - 1; t <= K; ++t)
+        if (K % t == 0) { T = t; break; }
+    g.T[a] = T;
+    g.nb[a] = K / T;
+    g.P[a] = T + J - 1;
   }
   int64_t stride = 1;
   g.nbins = 1;
@@ -841,7 +881,9 @@ int create_plan(int d, const int* Nd, const int* Kd, const int* Jd, int64_t M, c
     g.nbins *= g.nb[a];
     g.padded_cells *= g.P[a];
   }
-  if (g.padded_cells * (int64_t)sizeof(float2) > 200 * 1024)
+  // the gridding accumulates a padded tile in shared memory: two 32-bit words
+  // per cell (three in 3D)
+  if (g.padded_cells * (int64_t)(d == 3 ? 12 : 8) > 200 * 1024)
     return set_error(nullptr, NUFFT_EINVAL, "padded gridding tile of %lld cells exceeds shared memory; lower J",
                      (long long)g.padded_cells);
   if (g.nbins > 65536) return set_error(nullptr, NUFFT_EINVAL, "too many tiles (%lld)", (long long)g.nbins);
@@ -855,6 +897,11 @@ int create_plan(int d, const int* Nd, const int* Kd, const int* Jd, int64_t M, c
   p->Kprod = 1;
   for (int a = 0; a < d; ++a) { p->Nprod *= g.N[a]; p->Kprod *= g.K[a]; }
   p->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    delete p;
+    cudaGetLastError();
+    return set_error(nullptr, NUFFT_ECUDA, "cudaGetDevice failed");
+  }
   p->graphs_enabled = 1;
   snprintf(p->err, sizeof(p->err), "no error");
   const int rc = build_plan(p, om_dev);
@@ -895,8 +942,8 @@ extern "C" int nufft_plan_tuned(int d, const int* Nd, const int* Kd, const int* 
   float2 *xb = nullptr, *yb = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   auto cleanup = [&]() {
-    if (xb) cudaFree(xb);
-    if (yb) cudaFree(yb);
+    if (xb) dev_free(xb);
+    if (yb) dev_free(yb);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
   };
@@ -908,8 +955,8 @@ extern "C" int nufft_plan_tuned(int d, const int* Nd, const int* Kd, const int* 
       continue;
     }
     if (!xb) {
-      cudaError_t e = cudaMalloc((void**)&xb, p->Nprod * sizeof(float2));
-      if (e == cudaSuccess && p->M > 0) e = cudaMalloc((void**)&yb, p->M * sizeof(float2));
+      cudaError_t e = dev_malloc((void**)&xb, p->Nprod * sizeof(float2));
+      if (e == cudaSuccess && p->M > 0) e = dev_malloc((void**)&yb, p->M * sizeof(float2));
       if (e == cudaSuccess) e = cudaMemsetAsync(xb, 0, p->Nprod * sizeof(float2), st);
       if (e == cudaSuccess && yb) e = cudaMemsetAsync(yb, 0, p->M * sizeof(float2), st);
       if (e == cudaSuccess) e = cudaEventCreate(&e0);
@@ -962,8 +1009,8 @@ static void release_toeplitz(nufft_plan_t* p) {
     nufft_plan_destroy(p->toep_geom);
     p->toep_geom = nullptr;
   }
-  if (p->toep_T) cudaFree(p->toep_T);
-  if (p->toep_grid) cudaFree(p->toep_grid);
+  if (p->toep_T) dev_free(p->toep_T);
+  if (p->toep_grid) dev_free(p->toep_grid);
   p->toep_T = nullptr;
   p->toep_grid = nullptr;
   p->toep_cap = 0;

@@ -77,7 +77,7 @@ int get_aux(nufft_plan_t* p, float2** m0, float2** m1, float2** i0, float2** i1)
   const int64_t M = p->M > 0 ? p->M : 1;
   if (!p->mbuf) {
     const int64_t count = 2 * M + 2 * p->Nprod;
-    cudaError_t e = cudaMalloc((void**)&p->mbuf, count * sizeof(float2));
+    cudaError_t e = dev_malloc((void**)&p->mbuf, count * sizeof(float2));
     if (e != cudaSuccess) {
       p->mbuf = nullptr;
       return cuda_check(p, e, "auxiliary work space");

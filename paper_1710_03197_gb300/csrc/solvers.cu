@@ -49,7 +49,7 @@ int get_ws(nufft_plan_t* p, Ws* w) {
   const int64_t vec_bytes = ((n * (int64_t)sizeof(float2) + 255) / 256) * 256;
   const int64_t bytes = vec_bytes * V_COUNT + (int64_t)(2 * kDotBlocks + S_NSLOTS) * sizeof(double);
   if (!p->solver_ws) {
-    cudaError_t e = cudaMalloc(&p->solver_ws, bytes);
+    cudaError_t e = dev_malloc(&p->solver_ws, bytes);
     if (e != cudaSuccess) { p->solver_ws = nullptr; return cuda_check(p, e, "solver work space"); }
     p->solver_ws_bytes = bytes;
     p->device_bytes += bytes;
@@ -450,7 +450,7 @@ extern "C" int solve_cg_kspace(nufft_plan_t* p, const float* y_dev, float* x_dev
   const int64_t n = p->Kprod;
   const int64_t vb = ((n * (int64_t)sizeof(float2) + 255) / 256) * 256;
   if (!p->kspace_ws) {
-    cudaError_t e = cudaMalloc(&p->kspace_ws, 5 * vb);
+    cudaError_t e = dev_malloc(&p->kspace_ws, 5 * vb);
     if (e != cudaSuccess) { p->kspace_ws = nullptr; return cuda_check(p, e, "k-space CG work space"); }
     p->device_bytes += 5 * vb;
   }

@@ -60,7 +60,7 @@ __global__ void k_mul_spectrum(float2* grid, const float2* T, int64_t n, int nb)
 
 struct DevBuf {
   void* ptr = nullptr;
-  ~DevBuf() { if (ptr) cudaFree(ptr); }
+  ~DevBuf() { if (ptr) dev_free(ptr); }
 };
 struct PlanGuard {
   nufft_plan_t* p = nullptr;
@@ -71,10 +71,10 @@ int toeplitz_apply(nufft_plan_t* p, const float2* x, float2* out, int nb) {
   nufft_plan_t* tg = p->toep_geom;
   if (nb > p->toep_cap) {
     drop_graphs(p);   // graphs may reference the buffer freed below
-    if (p->toep_grid) cudaFree(p->toep_grid);
+    if (p->toep_grid) dev_free(p->toep_grid);
     p->toep_grid = nullptr;
     p->toep_cap = 0;
-    NUFFT_CUDA_TRY(p, cudaMalloc((void**)&p->toep_grid, (size_t)nb * tg->Kprod * sizeof(float2)));
+    NUFFT_CUDA_TRY(p, dev_malloc((void**)&p->toep_grid, (size_t)nb * tg->Kprod * sizeof(float2)));
     p->device_bytes += (int64_t)nb * tg->Kprod * (int64_t)sizeof(float2);
     p->toep_cap = nb;
   }
@@ -123,7 +123,7 @@ extern "C" int nufft_toeplitz_init(nufft_plan_t* p) {
   PlanGuard big, full, geom;
   const int64_t M = p->M;
   if (M > 0) {
-    NUFFT_CUDA_TRY(p, cudaMalloc(&om_rows.ptr, M * d * sizeof(float)));
+    NUFFT_CUDA_TRY(p, dev_malloc(&om_rows.ptr, M * d * sizeof(float)));
     k_om_rows<<<nblocks(M * d), kThreads, 0, st>>>(p->om_sorted, M, d, (float*)om_rows.ptr);
     NUFFT_CUDA_TRY(p, cudaGetLastError());
   }
@@ -132,11 +132,11 @@ extern "C" int nufft_toeplitz_init(nufft_plan_t* p) {
   int64_t n2 = 1;
   for (int a = 0; a < d; ++a) n2 *= N2[a];
   if (M > 0) {
-    NUFFT_CUDA_TRY(p, cudaMalloc(&ones.ptr, M * sizeof(float2)));
+    NUFFT_CUDA_TRY(p, dev_malloc(&ones.ptr, M * sizeof(float2)));
     k_fill<<<nblocks(M), kThreads, 0, st>>>((float2*)ones.ptr, M, make_float2(1.f, 0.f));
     NUFFT_CUDA_TRY(p, cudaGetLastError());
   }
-  NUFFT_CUDA_TRY(p, cudaMalloc(&x2.ptr, n2 * sizeof(float2)));
+  NUFFT_CUDA_TRY(p, dev_malloc(&x2.ptr, n2 * sizeof(float2)));
   rc = nufft_adjoint(big.p, (const float*)ones.ptr, (float*)x2.ptr);
   if (rc != NUFFT_OK) return set_error(p, rc, "Toeplitz kernel adjoint: %s", nufft_last_error(big.p));
   // T = DFT of the circular kernel.  A P image in a P grid is placed at
@@ -144,26 +144,26 @@ extern "C" int nufft_toeplitz_init(nufft_plan_t* p) {
   rc = nufft_plan(d, N2, K2, J, 0, nullptr, st, &full.p);
   if (rc != NUFFT_OK) return set_error(p, rc, "Toeplitz FFT plan: %s", nufft_last_error(nullptr));
   float2* T = nullptr;
-  NUFFT_CUDA_TRY(p, cudaMalloc((void**)&T, n2 * sizeof(float2)));
+  NUFFT_CUDA_TRY(p, dev_malloc((void**)&T, n2 * sizeof(float2)));
   rc = launch_fft_forward(full.p, (const float2*)x2.ptr, T, 1, false);
   if (rc != NUFFT_OK) {
-    cudaFree(T);
+    dev_free(T);
     return set_error(p, rc, "%s", full.p->err);
   }
   k_scale<<<nblocks(n2), kThreads, 0, st>>>(T, n2, (float)(1.0 / (double)n2));   // normalised inverse DFT
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
-    cudaFree(T);
+    dev_free(T);
     return cuda_check(p, e, "Toeplitz kernel scale");
   }
   rc = nufft_plan(d, Nn, K2, J, 0, nullptr, st, &geom.p);
   if (rc != NUFFT_OK) {
-    cudaFree(T);
+    dev_free(T);
     return set_error(p, rc, "Toeplitz geometry plan: %s", nufft_last_error(nullptr));
   }
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
-    cudaFree(T);
+    dev_free(T);
     return cuda_check(p, e, "Toeplitz kernel");
   }
   p->toep_T = T;

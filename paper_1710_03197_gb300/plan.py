@@ -44,7 +44,7 @@ class NufftPlan:
     """Min-max NUFFT plan for one trajectory (C: ``nufft_plan``).
 
     om: (M, d) float32 CUDA tensor of frequencies in radians; Nd, Kd, Jd: image
-    size, oversampled grid (powers of two) and neighbours per dimension.
+    size, oversampled grid (even, prime factors 2, 3, 5) and neighbours per dimension.
     """
 
     def __init__(self, om: torch.Tensor, Nd, Kd, Jd, stream=None, autotune: bool = False):

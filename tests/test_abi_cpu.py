@@ -29,8 +29,10 @@ def _plan(d, N, K, J, M=10, om=1):
 @pytest.mark.parametrize("d,N,K,J,M,om,frag", [
     (4, [8] * 4, [16] * 4, [4] * 4, 10, 1, "d = 4"),
     (0, [8], [16], [4], 10, 1, "d = 0"),
-    (2, [8, 8], [16, 100], [4, 4], 10, 1, "power of two"),
-    (2, [8, 8], [16, 2048], [4, 4], 10, 1, "power of two"),
+    (2, [8, 8], [16, 98], [4, 4], 10, 1, "prime factor"),      # 98 = 2 * 7^2
+    (2, [8, 8], [16, 2048], [4, 4], 10, 1, "in [16, 1024]"),
+    (2, [8, 8], [16, 45], [4, 4], 10, 1, "must be even"),       # odd K
+    (1, [8], [14], [4], 10, 1, "in [16, 1024]"),
     (2, [7, 8], [16, 16], [4, 4], 10, 1, "even"),
     (2, [32, 8], [16, 16], [4, 4], 10, 1, "even"),
     (2, [8, 8], [16, 16], [0, 4], 10, 1, "J[0]"),
@@ -40,6 +42,8 @@ def _plan(d, N, K, J, M=10, om=1):
     (3, [8, 8, 8], [16, 16, 16], [16, 16, 16], 10, 1, "shared memory"),
 ])
 def test_plan_rejects_bad_arguments(d, N, K, J, M, om, frag):
+    """Argument checks that run before any CUDA call.  Kd must be even, in
+    16..1024, with prime factors 2, 3 and 5 only (the FFT passes' radices)."""
     rc, h = _plan(d, N, K, J, M, om)
     assert rc == EINVAL
     assert not h.value

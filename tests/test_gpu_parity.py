@@ -61,6 +61,13 @@ CASES = [
     ("2d_spiral", (48, 48), (128, 128), (6, 6), lambda: W.spiral2d(8, 500)),
     ("3d_koosh", (24, 32, 16), (64, 64, 32), (6, 6, 6), lambda: W.kooshball3d(300, 64)),
     ("3d_mixedJ", (16, 16, 16), (32, 32, 32), (4, 5, 6), lambda: W.uniform_random_om(1500, 3, seed=25)),
+    # grids that are not powers of two (mixed-radix FFT passes, tiles of the
+    # largest power of two dividing K): 1.5x and 1.25x oversampling, a 1D grid
+    # of 2-cell tiles, factors 3 and 5 on different axes
+    ("2d_radial_K1.5", (256, 256), (384, 384), (6, 6), lambda: W.radial2d_golden(60, 384)),
+    ("3d_koosh_K1.25", (64, 64, 64), (80, 80, 80), (6, 6, 6), lambda: W.kooshball3d(300, 80)),
+    ("1d_K90", (40,), (90,), (6,), lambda: W.uniform_random_om(900, 1, seed=26)),
+    ("2d_K72x80_oddJ", (48, 60), (72, 80), (5, 6), lambda: W.uniform_random_om(4000, 2, seed=27)),
 ]
 
 
@@ -98,7 +105,11 @@ def test_tile_sort_and_bank_order(case):
     info = plan.info()
     d = len(case["Nd"])
     base = {1: 1024, 2: 16, 3: 16}[d]
-    T = [min(base, K) for K in case["Kd"]]
+
+    def edge(K, J):   # the largest divisor of K up to the base edge, else the smallest from J - 1 up
+        t = max(v for v in range(1, min(base, K) + 1) if K % v == 0)
+        return t if t >= J - 1 else min(v for v in range(J - 1, K + 1) if K % v == 0)
+    T = [edge(K, J) for K, J in zip(case["Kd"], case["Jd"])]
     nb = [K // t for K, t in zip(case["Kd"], T)]
     bins = np.zeros(M, dtype=np.int64)
     for a in range(d):
@@ -211,6 +222,49 @@ def test_selfadjoint_matches_oracle(case):
     assert rel(host(plan.selfadjoint(to_dev(x))), oracle.selfadjoint(ref, x)) < TOL_OP
 
 
+def test_gridding_operators_are_bit_identical_run_to_run(case):
+    """V^H accumulates in fixed point (integer atomics, a per-chunk power-of-two
+    scale from a fixed-order bound), so the order in which warps add has no
+    effect: repeated calls give bit-identical grids, adjoints and normal
+    operators."""
+    plan = case["plan"]
+    y = to_dev(cn(case["om"].shape[0], 10))
+    x = to_dev(cn(case["Nd"], 11))
+    for op, arg in ((plan.gridding, y), (plan.adjoint, y), (plan.selfadjoint, x)):
+        first = host(op(arg))
+        for _ in range(3):
+            np.testing.assert_array_equal(host(op(arg)), first)
+
+
+def test_dense_cluster_gridding_is_bit_identical_and_accurate(nf):
+    """The worst case for the fixed-point scale: thousands of random-phase samples
+    piled into one cell of a tile, so one chunk's bound is far above any single
+    contribution.  The grid still matches the oracle to the operator tolerance,
+    run after run identically, in 1D, 2D and 3D."""
+    rng = np.random.default_rng(90)
+    for Nd, Kd, Jd, n in (((64,), (128,), (6,), 4000), ((32, 32), (64, 64), (6, 6), 3000),
+                          ((16, 16, 16), (32, 32, 32), (6, 6, 6), 6000)):
+        d = len(Nd)
+        om = np.concatenate([(0.3 + 0.02 * rng.standard_normal((n, d))).astype(np.float32),
+                             W.uniform_random_om(300, d, seed=91)])
+        ref = oracle.make_plan(om, Nd, Kd, Jd)
+        y = cn(om.shape[0], 92)
+        y[:5] *= 1e3                               # a few large samples set the chunk's scale
+        with nf.NufftPlan(to_dev(om), Nd, Kd, Jd) as plan:
+            Z = host(plan.gridding(to_dev(y)))
+            np.testing.assert_array_equal(host(plan.gridding(to_dev(y))), Z)
+        assert rel(Z, oracle.gridding_VH(ref, y)) < TOL_OP, (d, rel(Z, oracle.gridding_VH(ref, y)))
+
+
+def test_gridding_propagates_non_finite_samples(nf):
+    om = W.uniform_random_om(500, 2, seed=93)
+    y = cn(500, 94)
+    y[7] = np.inf
+    with nf.NufftPlan(to_dev(om), (16, 16), (32, 32), (6, 6)) as plan:
+        Z = host(plan.gridding(to_dev(y)))
+    assert np.isnan(Z).any()
+
+
 @pytest.mark.parametrize("Nd,Kd,Jd,gen", [
     ((64, 64), (128, 128), (6, 6), lambda: W.radial2d_uniform(64, 128)),
     ((24, 40), (64, 128), (6, 6), lambda: W.uniform_random_om(3001, 2, seed=22)),
@@ -223,8 +277,8 @@ def test_fused_normal_operator_equals_forward_then_adjoint(nf, Nd, Kd, Jd, gen):
     """2D A^H A runs V^H V as one gather-then-scatter pass per tile chunk (1D
     and 3D run V then V^H); it
     must agree with the separate forward and adjoint calls (the same
-    arithmetic up to the gridding's atomic summation order), singly and
-    batched."""
+    arithmetic up to the float rounding of the gathered samples), singly and
+    batched; the batched form is bit-identical run to run."""
     om = gen()
     with nf.NufftPlan(to_dev(om), Nd, Kd, Jd) as plan:
         xs = [cn(Nd, 80 + b) for b in range(3)]
@@ -234,6 +288,7 @@ def test_fused_normal_operator_equals_forward_then_adjoint(nf, Nd, Kd, Jd, gen):
             assert rel(host(plan.selfadjoint(xd)), two) < 1e-6
         xb = to_dev(np.stack(xs))
         outb = host(plan.selfadjoint_batch(xb))
+        np.testing.assert_array_equal(host(plan.selfadjoint_batch(xb)), outb)
         for b, x in enumerate(xs):
             two = host(plan.adjoint(plan.forward(to_dev(x))))
             assert rel(outb[b], two) < 1e-6
@@ -264,9 +319,8 @@ def test_golden_nudft_fixture(nf):
 
 # ------------------------------------------------------------------ full-size workloads
 
-def test_full_2d_256_forward_adjoint_elementwise(nf):
-    spec, om, x, noise = W.make_workload("radial2d_256")
-    ref = oracle.make_plan(om, spec["Nd"], spec["Kd"], spec["Jd"])
+def test_full_2d_256_forward_adjoint_elementwise(nf, oracle_workload):
+    spec, om, x, noise, ref = oracle_workload("radial2d_256")
     with nf.NufftPlan(to_dev(om), spec["Nd"], spec["Kd"], spec["Jd"]) as plan:
         y = host(plan.forward(to_dev(x)))
         y_in = (oracle.forward(ref, x) + noise).astype(np.complex64)
@@ -300,6 +354,26 @@ def test_full_3d_128_forward_sampled_and_identities(nf):
         aha = host(plan.selfadjoint(xd))
         ah_ax = host(plan.adjoint(y))
         assert rel(aha, ah_ax) < 1e-6
+
+
+def test_full_3d_128_adjoint_on_a_point_subset_elementwise(nf):
+    """The full kooshball plan (2.1M points, every chunk and tile of the
+    workload) applied to samples that are zero except on ~3,500 points,
+    including the 500 nearest the centre, where the tiles are densest and are
+    cut into several chunks.  Zero samples add nothing, so the exact result is
+    the oracle's adjoint on those points alone, checked element by element
+    over the whole 128^3 image."""
+    spec, om, x, _ = W.make_workload("kooshball3d_128")
+    rng = np.random.default_rng(33)
+    centre = np.argsort(np.abs(om.astype(np.float64)).sum(1))[:500]
+    idx = np.unique(np.concatenate([rng.choice(om.shape[0], 3000, replace=False), centre, [0, om.shape[0] - 1]]))
+    v = np.zeros(om.shape[0], dtype=np.complex64)
+    v[idx] = cn(idx.size, 34)
+    with nf.NufftPlan(to_dev(om), spec["Nd"], spec["Kd"], spec["Jd"]) as plan:
+        assert plan.info()["nchunks"] > plan.info()["nbins"] // 2
+        xa = host(plan.adjoint(to_dev(v)))
+    ref_s = oracle.make_plan(om[idx], spec["Nd"], spec["Kd"], spec["Jd"])
+    assert rel(xa, oracle.adjoint(ref_s, v[idx])) < TOL_OP
 
 
 # ------------------------------------------------------------------ solvers

@@ -171,6 +171,8 @@ WORKLOADS = {
     "radial2d_256": dict(d=2, Nd=(256, 256), Kd=(512, 512), Jd=(6, 6)),
     # 3D 128^3 -> 256^3, J=6, kooshball 8192 spokes x 256 samples (2,097,152 points)
     "kooshball3d_128": dict(d=3, Nd=(128, 128, 128), Kd=(256, 256, 256), Jd=(6, 6, 6)),
+    # the same 2D radial workload on a 1.5x oversampled 384x384 grid (a size with a factor 3)
+    "radial2d_256_K384": dict(d=2, Nd=(256, 256), Kd=(384, 384), Jd=(6, 6)),
     # 2D 256x256 -> 512x512, J=6, 16 spiral interleaves x 2048 samples, om + N(0, 1e-3) rad (32,768 points)
     "spiral2d_256": dict(d=2, Nd=(256, 256), Kd=(512, 512), Jd=(6, 6)),
 }
@@ -183,7 +185,7 @@ def make_workload(name: str):
         om = radial2d_uniform(64, 128)
         x = complex_normal_image(spec["Nd"])
         noise = None
-    elif name == "radial2d_256":
+    elif name in ("radial2d_256", "radial2d_256_K384"):
         om = radial2d_golden(403, 512)
         x = ellipse_phantom(256)
         noise = complex_noise(om.shape[0], 0.1)
