@@ -694,22 +694,133 @@ def _oracle_setup(name="radial2d_256"):
     return oracle, spec, plan, x
 
 
-def cpu_baseline(seconds: float = 10.0):
-    """The FP64 oracle's forward + adjoint on the full 2D workload, timed on the
-    host (plan precompute excluded), repeated until ``seconds`` have elapsed."""
-    oracle, spec, plan, x = _oracle_setup()
-    reps, t0, c0 = 0, time.perf_counter(), time.process_time()
+def _oracle_pair(oracle, plan, x):
+    y = oracle.forward(plan, x)
+    oracle.adjoint(plan, y)
+
+
+def _cpu_worker(name, lo, hi, slot, shm_names, conn):
+    """One process of the all-cores baseline: the oracle's V and V^H for the
+    points [lo, hi) of the workload, on data in shared memory."""
+    from multiprocessing import shared_memory
+    import oracle
+    spec, om, _, _ = W.make_workload(name)
+    plan = oracle.make_plan(om[lo:hi], spec["Nd"], spec["Kd"], spec["Jd"])
+    M, Kd = spec["M"], tuple(spec["Kd"])
+    shms = [shared_memory.SharedMemory(name=n) for n in shm_names]
+    Y = np.ndarray(Kd, dtype=np.complex128, buffer=shms[0].buf)
+    y = np.ndarray((M,), dtype=np.complex128, buffer=shms[1].buf)
+    Z = np.ndarray(Kd, dtype=np.complex128, buffer=shms[2].buf, offset=slot * int(np.prod(Kd)) * 16)
+    conn.send("ready")
     while True:
-        y = oracle.forward(plan, x)
-        oracle.adjoint(plan, y)
-        reps += 1
-        el = time.perf_counter() - t0
-        if el >= seconds:
+        cmd = conn.recv()
+        if cmd == "V":
+            y[lo:hi] = oracle.interp_V(plan, Y)
+        elif cmd == "VH":
+            Z[...] = oracle.gridding_VH(plan, y[lo:hi])
+        else:
             break
-    cores = max(1, round((time.process_time() - c0) / el))   # threads the timed loop kept busy
-    return {"value": round(spec["M"] * reps / el, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{reps} forward+adjoint pairs on the full radial2d_256 workload (206,336 points), "
-                      f"FP64 numpy, plan excluded, {el:.1f} s"}
+        conn.send("done")
+    for sh in shms:
+        sh.close()
+
+
+def _cpu_all_cores(name, cores, pairs):
+    """The oracle's forward + adjoint with V and V^H split over `cores`
+    processes by point range (S, F, F^H and the crop in this process):
+    median seconds per pair over `pairs` pairs."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    import oracle
+    spec, om, x, _ = W.make_workload(name)
+    M, Kd = spec["M"], tuple(spec["Kd"])
+    kprod = int(np.prod(Kd))
+    plan0 = oracle.make_plan(om[:1], spec["Nd"], spec["Kd"], spec["Jd"])   # S only depends on N, K, J
+    shms = [shared_memory.SharedMemory(create=True, size=kprod * 16),
+            shared_memory.SharedMemory(create=True, size=M * 16),
+            shared_memory.SharedMemory(create=True, size=cores * kprod * 16)]
+    ctx = mp.get_context("spawn")
+    bounds = np.linspace(0, M, cores + 1).astype(int)
+    procs, conns = [], []
+    try:
+        for c in range(cores):
+            a, b = ctx.Pipe()
+            pr = ctx.Process(target=_cpu_worker, args=(name, int(bounds[c]), int(bounds[c + 1]), c,
+                                                        [sh.name for sh in shms], b))
+            pr.start()
+            procs.append(pr)
+            conns.append(a)
+        for cn in conns:
+            assert cn.recv() == "ready"
+        Y = np.ndarray(Kd, dtype=np.complex128, buffer=shms[0].buf)
+        Zs = np.ndarray((cores,) + Kd, dtype=np.complex128, buffer=shms[2].buf)
+
+        def pair():
+            Y[...] = oracle.fft_forward(oracle.scale_pad(plan0, x))
+            for cmd in ("V", "VH"):
+                for cn in conns:
+                    cn.send(cmd)
+                for cn in conns:
+                    assert cn.recv() == "done"
+            Z = Zs[0].copy()
+            for c in range(1, cores):
+                Z += Zs[c]
+            oracle.crop_rescale(plan0, oracle.fft_adjoint(Z))
+
+        pair()
+        ts = []
+        for _ in range(pairs):
+            t0 = time.perf_counter()
+            pair()
+            ts.append(time.perf_counter() - t0)
+        for cn in conns:
+            cn.send("quit")
+        for pr in procs:
+            pr.join(timeout=30)
+        return statistics.median(ts)
+    finally:
+        for pr in procs:
+            if pr.is_alive():
+                pr.terminate()
+        for sh in shms:
+            sh.close()
+            sh.unlink()
+
+
+def cpu_baseline(seconds: float = 10.0, pairs: int = 20):
+    """The FP64 oracle's forward + adjoint on the full 2D workload, timed on the
+    host (plan precompute excluded): the median of `pairs` timed pairs on one
+    core (the oracle as it stands), and the same with V and V^H split by point
+    range over all host cores.  `seconds` caps the one-core sample."""
+    oracle, spec, plan, x = _oracle_setup()
+    _oracle_pair(oracle, plan, x)
+    ts, t_start = [], time.perf_counter()
+    for _ in range(pairs):
+        t0 = time.perf_counter()
+        _oracle_pair(oracle, plan, x)
+        ts.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start > seconds:
+            break
+    one = statistics.median(ts)
+    cores = os.cpu_count() or 1
+    try:
+        allc = _cpu_all_cores("radial2d_256", cores, pairs)
+    except Exception as exc:   # report, do not fail the bench
+        allc, err = None, str(exc).splitlines()[0][:200] if str(exc) else type(exc).__name__
+    else:
+        err = None
+    M = spec["M"]
+    line = {"value": round(M / allc, 1) if allc else round(M / one, 1), "unit": UNIT,
+            "cores": cores if allc else 1, "kind": "oracle",
+            "sample": f"median of {len(ts)} (one core) and {pairs} (all cores) forward+adjoint pairs on the full "
+                      "radial2d_256 workload (206,336 points), FP64 numpy, plan excluded; all cores: V and V^H "
+                      f"split by point range over {cores} processes, S, F, F^H and the crop in one",
+            "single_core": {"value": round(M / one, 1), "unit": UNIT, "cores": 1, "median_pair_s": round(one, 4)}}
+    if allc:
+        line["all_cores_median_pair_s"] = round(allc, 4)
+    if err:
+        line["all_cores_error"] = err
+    return line
 
 
 def reference(args):

@@ -108,6 +108,213 @@ k_interp(const float2* __restrict__ grid_b, float2* __restrict__ y_b, const Poin
   if (active && l == 0) y[P.perm[i]] = tot;
 }
 
+// ---------------------------------------------------------------- interpolation, per chunk
+// One CTA per chunk of a tile's points (3D; 2D below).  The chunk's padded tile of
+// the grid ((T+J-1)^d cells, wrapped at the grid edge) is copied into shared
+// memory once, as a plane of real parts and a plane of imaginary parts, and
+// every point gathers its J^d neighbours from there instead of from global
+// memory.  The plan orders each chunk so that the points sharing a warp
+// instruction read disjoint bank windows of these planes (the gridding uses
+// the same order for its atomics).  Lane layout, arithmetic and summation
+// order are those of k_interp, so the results are identical.
+template <int D>
+struct InterpChunkCfg {
+  static constexpr int kThreads = D == 3 ? 512 : 256;
+  static constexpr int kMinBlocks = D == 3 ? 2 : 4;
+};
+
+template <int D, int JF, int TF>
+__global__ void __launch_bounds__(InterpChunkCfg<D>::kThreads, InterpChunkCfg<D>::kMinBlocks)
+k_interp_chunk(const float2* __restrict__ grid_b, float2* __restrict__ y_b, const Chunk* __restrict__ chunks,
+               const Points P, const Geom g, int64_t gbs, int64_t ybs) {
+  static_assert(TF == 0 || JF > 0, "a fixed tile needs a fixed J");
+  constexpr int PF = TF > 0 ? TF + JF - 1 : 0;
+  extern __shared__ float tile[];
+  const float2* __restrict__ grid = grid_b + (int64_t)blockIdx.y * gbs;
+  float2* __restrict__ y = y_b + (int64_t)blockIdx.y * ybs;
+  const int ncell = TF > 0 ? (D == 2 ? PF * PF : PF * PF * PF) : (int)g.padded_cells;
+  const int P1 = TF > 0 ? PF : g.P[1];
+  const int P2 = D > 2 ? (TF > 0 ? PF : g.P[2]) : 1;
+  float* gre = tile;
+  float* gim = tile + ncell;
+  const Chunk ch = chunks[blockIdx.x];
+  int org[kMaxDim];
+  {
+    int rem = ch.bin;
+    for (int a = D - 1; a >= 0; --a) {
+      org[a] = (rem % g.nb[a]) * g.T[a];
+      rem /= g.nb[a];
+    }
+  }
+  // the padded tile, cell c = (r0, r1[, r2]) in C order with pitches P
+  for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+    int r0, r1, r2 = 0;
+    if (D == 2) {
+      r1 = c % P1;
+      r0 = c / P1;
+    } else {
+      r2 = c % P2;
+      r1 = (c / P2) % P1;
+      r0 = c / (P2 * P1);
+    }
+    int64_t gi = (int64_t)wrapk(org[0] + r0, g.K[0]) * g.Kstride[0] + (int64_t)wrapk(org[1] + r1, g.K[1]) * g.Kstride[1];
+    if (D == 3) gi += wrapk(org[2] + r2, g.K[2]);
+    const float2 v = __ldg(&grid[gi]);
+    gre[c] = v.x;
+    gim[c] = v.y;
+  }
+  __syncthreads();
+
+  const int G = JF > 0 ? JF : g.J[D - 1];
+  const int lane = threadIdx.x & 31;
+  const int per_warp = 32 / G;
+  const int sub = lane / G;
+  const int l = lane - sub * G;
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const int J0 = JF > 0 ? JF : g.J[0];
+  const int J1 = JF > 0 ? JF : (D > 2 ? g.J[1] : 1);
+  // warp-uniform rounds of per_warp points (the lane-group sum is a full-warp shuffle)
+  for (int qb = warp * per_warp; qb < ch.count; qb += nwarps * per_warp) {
+    const int q = qb + sub;
+    const bool act = (sub < per_warp) && (q < ch.count);
+    const int64_t i = (int64_t)ch.start + q;
+    float2 part = make_float2(0.f, 0.f);
+    if (act) {
+      const int ll = P.kf[(int64_t)(D - 1) * P.M + i] - org[D - 1] + l;
+      const float2 cl = P.coef[P.coef_off[D - 1] + (int64_t)l * P.M + i];
+      const int l0 = P.kf[i] - org[0];
+      float2 acc = make_float2(0.f, 0.f);
+      if (D == 2) {
+#pragma unroll
+        for (int j0 = 0; j0 < (JF > 0 ? JF : kMaxJ); ++j0) {
+          if (JF == 0 && j0 >= J0) break;
+          const float2 c0 = P.coef[P.coef_off[0] + (int64_t)j0 * P.M + i];
+          const int cell = (l0 + j0) * P1 + ll;
+          acc = cadd(acc, cmul(c0, make_float2(gre[cell], gim[cell])));
+        }
+      } else {
+        const int l1 = P.kf[P.M + i] - org[1];
+        float2 c1v[JF > 0 ? JF : kMaxJ];
+#pragma unroll
+        for (int j1 = 0; j1 < (JF > 0 ? JF : kMaxJ); ++j1) {
+          if (JF == 0 && j1 >= J1) break;
+          c1v[j1] = P.coef[P.coef_off[1] + (int64_t)j1 * P.M + i];
+        }
+        constexpr int kU0 = TF > 0 ? JF : 1;
+#pragma unroll kU0
+        for (int j0 = 0; j0 < J0; ++j0) {
+          const float2 c0 = P.coef[P.coef_off[0] + (int64_t)j0 * P.M + i];
+          const int rowbase = ((l0 + j0) * P1 + l1) * P2 + ll;
+          float2 acc1 = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int j1 = 0; j1 < (JF > 0 ? JF : kMaxJ); ++j1) {
+            if (JF == 0 && j1 >= J1) break;
+            const int cell = rowbase + j1 * P2;
+            acc1 = cadd(acc1, cmul(c1v[j1], make_float2(gre[cell], gim[cell])));
+          }
+          acc = cadd(acc, cmul(c0, acc1));
+        }
+      }
+      part = cmul(cl, acc);
+    }
+    const int base = sub * G;
+    float2 tot = make_float2(0.f, 0.f);
+    for (int r = 0; r < G; ++r) {
+      const int src = (base + r) & 31;
+      tot.x += __shfl_sync(0xffffffffu, part.x, src);
+      tot.y += __shfl_sync(0xffffffffu, part.y, src);
+    }
+    if (act && l == 0) y[P.perm[i]] = tot;
+  }
+}
+
+// 2D: the chunk's point data are staged too (one thread per point: first
+// neighbours, the J0 + J1 coefficients and the permutation), so the CTA waits
+// for one round of global loads instead of one per pass of its warps over the
+// chunk; the gathers then read only shared memory.  Shared memory: the two
+// planes of the padded tile, c0[J0][cap], c1[cap][J1] (as in the gridding's
+// staged kernel), k[2][cap], perm[cap].
+template <int JF>
+__global__ void __launch_bounds__(256, 4)
+k_interp_chunk2d(const float2* __restrict__ grid_b, float2* __restrict__ y_b, const Chunk* __restrict__ chunks,
+                 const Points P, const Geom g, int64_t gbs, int64_t ybs) {
+  constexpr int cap = kChunkPoints[2];
+  static_assert(cap == 256, "one thread per staged point");
+  extern __shared__ float tile[];
+  const float2* __restrict__ grid = grid_b + (int64_t)blockIdx.y * gbs;
+  float2* __restrict__ y = y_b + (int64_t)blockIdx.y * ybs;
+  const int ncell = (int)g.padded_cells;
+  const int P1 = g.P[1];
+  const int J0 = JF > 0 ? JF : g.J[0];
+  const int J1 = JF > 0 ? JF : g.J[1];
+  float* gre = tile;
+  float* gim = tile + ncell;
+  float2* s_c = reinterpret_cast<float2*>(tile + 2 * ncell);   // 8-byte aligned: 2 * ncell floats
+  int* s_k = reinterpret_cast<int*>(s_c + (J0 + J1) * cap);
+  int* s_p = s_k + 2 * cap;
+  const Chunk ch = chunks[blockIdx.x];
+  const int org0 = ((ch.bin / g.nb[1]) % g.nb[0]) * g.T[0];
+  const int org1 = (ch.bin % g.nb[1]) * g.T[1];
+  for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+    const int r1 = c % P1, r0 = c / P1;
+    const float2 v = __ldg(&grid[(int64_t)wrapk(org0 + r0, g.K[0]) * g.Kstride[0] + wrapk(org1 + r1, g.K[1])]);
+    gre[c] = v.x;
+    gim[c] = v.y;
+  }
+  const int qs = threadIdx.x;
+  if (qs < ch.count) {
+    const int64_t i = (int64_t)ch.start + qs;
+    s_p[qs] = P.perm[i];
+    s_k[qs] = P.kf[i] - org0;
+    s_k[cap + qs] = P.kf[P.M + i] - org1;
+#pragma unroll
+    for (int r = 0; r < (JF > 0 ? JF : kMaxJ); ++r) {
+      if (JF == 0 && r >= J0) break;
+      s_c[r * cap + qs] = P.coef[P.coef_off[0] + (int64_t)r * P.M + i];
+    }
+#pragma unroll
+    for (int r = 0; r < (JF > 0 ? JF : kMaxJ); ++r) {
+      if (JF == 0 && r >= J1) break;
+      s_c[J0 * cap + qs * J1 + r] = P.coef[P.coef_off[1] + (int64_t)r * P.M + i];
+    }
+  }
+  __syncthreads();
+
+  const int G = J1;
+  const int lane = threadIdx.x & 31;
+  const int per_warp = 32 / G;
+  const int sub = lane / G;
+  const int l = lane - sub * G;
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  for (int qb = warp * per_warp; qb < ch.count; qb += nwarps * per_warp) {
+    const int q = qb + sub;
+    const bool act = (sub < per_warp) && (q < ch.count);
+    float2 part = make_float2(0.f, 0.f);
+    if (act) {
+      const int ll = s_k[cap + q] + l;
+      const int l0 = s_k[q];
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j0 = 0; j0 < (JF > 0 ? JF : kMaxJ); ++j0) {
+        if (JF == 0 && j0 >= J0) break;
+        const int cell = (l0 + j0) * P1 + ll;
+        acc = cadd(acc, cmul(s_c[j0 * cap + q], make_float2(gre[cell], gim[cell])));
+      }
+      part = cmul(s_c[J0 * cap + q * J1 + l], acc);
+    }
+    const int base = sub * G;
+    float2 tot = make_float2(0.f, 0.f);
+    for (int r = 0; r < G; ++r) {
+      const int src = (base + r) & 31;
+      tot.x += __shfl_sync(0xffffffffu, part.x, src);
+      tot.y += __shfl_sync(0xffffffffu, part.y, src);
+    }
+    if (act && l == 0) y[s_p[q]] = tot;
+  }
+}
+
 // ---------------------------------------------------------------- gridding, per chunk
 // Deterministic accumulation.  The points of a chunk add into a shared copy
 // of the padded tile in fixed point: every contribution is scaled by a power
@@ -499,10 +706,12 @@ k_gridding_reduce(const float2* __restrict__ tiles_b, const int32_t* __restrict_
 // points hit distinct bank pairs), y[cap], k[2][cap] (first neighbours
 // relative to the tile origin), cap = chunk size.
 // FUSED (V^H V, the normal operator's grid part): y_b is the oversampled
-// spectrum instead of the samples; each point's y is first gathered from it
-// into shared memory (the interpolation's arithmetic and summation order, in
-// the scatter's lane layout), so the samples never leave the CTA and the
-// coefficients are read once for both directions.
+// spectrum instead of the samples; the chunk's padded tile of it is staged in
+// shared memory (two float planes after the point data), and each point's y is
+// first gathered from there into shared memory (the interpolation's
+// arithmetic and summation order, in the scatter's lane layout), so the
+// samples never leave the CTA and the coefficients are read once for both
+// directions.
 template <int JF, bool FUSED>
 __global__ void __launch_bounds__(256, 4)
 k_gridding_chunk_staged(const float2* __restrict__ y_b, float2* __restrict__ tiles_b,
@@ -518,11 +727,22 @@ k_gridding_chunk_staged(const float2* __restrict__ y_b, float2* __restrict__ til
   float2* s_c = reinterpret_cast<float2*>(acc + 2 * ncell);   // 8-byte aligned: 2 * ncell words
   float2* s_y = s_c + (J0 + J1) * cap;
   int* s_k = reinterpret_cast<int*>(s_y + cap);
+  float* gre = reinterpret_cast<float*>(s_k + 2 * cap);   // FUSED: the chunk's padded tile of the spectrum
+  float* gim = gre + ncell;
   const Chunk ch = chunks[blockIdx.x];
   const int org0 = ((ch.bin / g.nb[1]) % g.nb[0]) * g.T[0];
   const int org1 = (ch.bin % g.nb[1]) * g.T[1];
 
   for (int c = threadIdx.x; c < 2 * ncell; c += blockDim.x) acc[c] = 0;
+  if (FUSED) {
+    const int P1 = g.P[1];
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+      const int r1 = c % P1, r0 = c / P1;
+      const float2 v = __ldg(&y[(int64_t)wrapk(org0 + r0, g.K[0]) * g.Kstride[0] + wrapk(org1 + r1, g.K[1])]);
+      gre[c] = v.x;
+      gim[c] = v.y;
+    }
+  }
   static_assert(cap == 256, "one thread per staged point");
   const int qs = threadIdx.x;           // the point this thread stages
   int pm = 0;
@@ -556,20 +776,20 @@ k_gridding_chunk_staged(const float2* __restrict__ y_b, float2* __restrict__ til
   const int P1 = g.P[1];
   if (FUSED) {
     // warp-uniform rounds of per_warp points: the lane-group sum is a
-    // full-warp shuffle
-    const int ks0 = (int)g.Kstride[0];
+    // full-warp shuffle; the spectrum is read from the staged tile
     for (int qb = warp * per_warp; qb < ch.count; qb += nwarps * per_warp) {
       const int q = qb + sub;
       const bool act = (sub < per_warp) && (q < ch.count);
       float2 part = make_float2(0.f, 0.f);
       if (act) {
-        const int gl = wrapk(s_k[cap + q] + org1 + l, g.K[1]);
-        const int k0 = s_k[q] + org0;
+        const int ll = s_k[cap + q] + l;
+        const int l0 = s_k[q];
         float2 a = make_float2(0.f, 0.f);
 #pragma unroll
         for (int j0 = 0; j0 < (JF > 0 ? JF : kMaxJ); ++j0) {
           if (JF == 0 && j0 >= J0) break;
-          a = cadd(a, cmul(s_c[j0 * cap + q], __ldg(&y[wrapk(k0 + j0, g.K[0]) * ks0 + gl])));
+          const int cell = (l0 + j0) * P1 + ll;
+          a = cadd(a, cmul(s_c[j0 * cap + q], make_float2(gre[cell], gim[cell])));
         }
         part = cmul(s_c[J0 * cap + q * J1 + l], a);
       }
@@ -634,7 +854,40 @@ bool all_j_equal(const Geom& g, int J) {
 }
 
 template <int D>
+cudaError_t interp_chunks(const nufft_plan_t* p, const float2* grid, float2* y, int nb) {
+  if (p->nchunks == 0) return cudaSuccess;
+  const Points P = points_view(p);
+  const dim3 gd((unsigned)p->nchunks, (unsigned)nb);
+  const bool j6 = all_j_equal(p->g, 6);
+  bool t16 = true;
+  for (int a = 0; a < D; ++a) t16 = t16 && p->g.T[a] == 16;
+  if constexpr (D == 2) {
+    const int sj = p->g.J[0] + p->g.J[1];
+    const size_t smem = (size_t)p->g.padded_cells * 2 * sizeof(float) +
+                        (size_t)kChunkPoints[2] * ((size_t)sj * sizeof(float2) + 3 * sizeof(int));
+    auto kern = j6 ? k_interp_chunk2d<6> : k_interp_chunk2d<0>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<gd, kChunkPoints[2], smem, p->stream>>>(grid, y, p->chunks, P, p->g, p->Kprod, p->M);
+    return cudaGetLastError();
+  } else {
+    const size_t smem = (size_t)p->g.padded_cells * 2 * sizeof(float);
+    auto kern = j6 ? (t16 ? k_interp_chunk<D, 6, 16> : k_interp_chunk<D, 6, 0>) : k_interp_chunk<D, 0, 0>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<gd, InterpChunkCfg<D>::kThreads, smem, p->stream>>>(grid, y, p->chunks, P, p->g, p->Kprod, p->M);
+    return cudaGetLastError();
+  }
+}
+
+template <int D>
 cudaError_t interp_d(const nufft_plan_t* p, const float2* grid, float2* y, int nb) {
+  // single transforms gather from staged tiles; a batch keeps the per-point
+  // kernel (the chunk kernel would stage each chunk's point data once per
+  // batch element: the 32-coil frames' normal operator measured 2.36 -> 2.87 ms)
+  if constexpr (D > 1) {
+    if (nb == 1) return interp_chunks<D>(p, grid, y, nb);
+  }
   const Points P = points_view(p);
   const int G = p->g.J[D - 1];
   const int per_warp = 32 / G;
@@ -659,7 +912,8 @@ cudaError_t launch_chunks(const nufft_plan_t* p, const float2* y, float2* tiles,
   if constexpr (D == 2) {
     const int sj = p->g.J[0] + p->g.J[1];
     const size_t smem = (size_t)p->g.padded_cells * Fix<2>::kWords * sizeof(int) +
-                        (size_t)kChunkPoints[2] * ((size_t)sj * sizeof(float2) + sizeof(float2) + 2 * sizeof(int));
+                        (size_t)kChunkPoints[2] * ((size_t)sj * sizeof(float2) + sizeof(float2) + 2 * sizeof(int)) +
+                        (FUSED ? (size_t)p->g.padded_cells * 2 * sizeof(float) : 0);
     auto kern = j6 ? k_gridding_chunk_staged<6, FUSED> : k_gridding_chunk_staged<0, FUSED>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -13,6 +13,7 @@
 // CTA summing the per-CTA results), so a solve is reproducible for a given
 // operator output.  Scalars stay in device memory: no host round trip per
 // iteration.
+#include <algorithm>
 #include <vector>
 
 #include "internal.cuh"
@@ -28,7 +29,7 @@ using namespace nufft;
 
 namespace {
 
-constexpr int kDotBlocks = 608;      // 4 x 152 SMs
+constexpr int kDotBlocks = 304;      // 2 x 152 SMs: one 256-thread CTA per 256 elements of a 256^2 image
 constexpr int kDotThreads = 256;
 constexpr int kEwThreads = 256;
 
@@ -63,14 +64,18 @@ int get_ws(nufft_plan_t* p, Ws* w) {
 
 // --------------------------------------------------------------- reductions
 __device__ __forceinline__ double block_sum(double v) {
-  __shared__ double red[kDotThreads];
-  red[threadIdx.x] = v;
+  // a fixed shuffle tree in each warp, then the warps' sums in warp order;
+  // every thread returns the same value
+  __shared__ double red[kDotThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  for (int s = kDotThreads / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-    __syncthreads();
-  }
-  return red[0];
+  double t = 0.0;
+#pragma unroll
+  for (int w = 0; w < kDotThreads / 32; ++w) t += red[w];
+  __syncthreads();   // red free for the next call
+  return t;
 }
 
 // part[b] = sum over this CTA's strided share of Re(conj(a) b)
@@ -94,14 +99,12 @@ __global__ void __launch_bounds__(kDotThreads) k_dot_final(const double* part, d
 // --------------------------------------------------------------- CG vector steps
 __device__ __forceinline__ double safe_div(double a, double b) { return b != 0.0 ? a / b : 0.0; }
 
-// Sum of the kDotBlocks partial sums, in the same order in every CTA (so
-// every CTA of a kernel gets the same value).
-__device__ __forceinline__ double sum_partials(const double* part) {
+// Sum of the first `count` partial sums (kDotBlocks by default), in the same
+// order in every CTA (so every CTA of a kernel gets the same value).
+__device__ __forceinline__ double sum_partials(const double* part, int count = kDotBlocks) {
   double s = 0.0;
-  for (int i = threadIdx.x; i < kDotBlocks; i += kDotThreads) s += part[i];
-  const double t = block_sum(s);
-  __syncthreads();   // block_sum's scratch is reused by the caller
-  return t;
+  for (int i = threadIdx.x; i < count; i += kDotThreads) s += part[i];
+  return block_sum(s);
 }
 
 // x += alpha p, r -= alpha q, alpha = rr / <p, q> (<p, q> summed here from its

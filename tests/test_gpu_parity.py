@@ -420,49 +420,6 @@ def test_cg_5_iterations_radial2d_64(nf):
     assert rel(xg, oracle.cg(ref, y, np.zeros(spec["Nd"]), 5)) < TOL_SOLVER
 
 
-def _envelope(monkeypatch, run_oracle, op_err, seeds=(1, 2)):
-    """Spread of an oracle solve when its normal operator A^H A is perturbed by
-    relative Gaussian noise of size op_err (the GPU operator's measured error)."""
-    import oracle.solvers as S
-    exact = S.selfadjoint
-    ref = run_oracle()
-    spread = 0.0
-    for seed in seeds:
-        rng = np.random.default_rng(seed)
-
-        def noisy(plan_, vv, rng=rng):
-            out = exact(plan_, vv)
-            return out * (1 + op_err * rng.standard_normal(out.shape))
-        monkeypatch.setattr(S, "selfadjoint", noisy)
-        try:
-            spread = max(spread, rel(run_oracle(), ref))
-        finally:
-            monkeypatch.setattr(S, "selfadjoint", exact)
-    return ref, spread
-
-
-def _op_err(plan, ref, Nd):
-    v = cn(Nd, 60)
-    return rel(host(plan.selfadjoint(to_dev(v))), oracle.selfadjoint(ref, v))
-
-
-def test_cg_20_iterations_radial2d_64_within_fp32_envelope(nf, monkeypatch):
-    """20 CG iterations on the 64^2 radial problem amplify FP32 rounding about
-    1e4-fold (the oracle itself moves by ~1e-2 when its operator output is
-    perturbed at 1e-6), so the bound is derived from the arithmetic: the GPU
-    iterate must lie within 3x the spread of oracle runs whose normal operator
-    is perturbed by relative noise of the GPU operator's own measured error."""
-    spec, om, ref, y = _solver_problem("radial2d_64")
-    Nd = spec["Nd"]
-    with nf.NufftPlan(to_dev(om), Nd, spec["Kd"], spec["Jd"]) as plan:
-        xg = host(plan.solve_cg(to_dev(y), maxiter=20))
-        op_err = _op_err(plan, ref, Nd)
-    assert op_err < TOL_OP
-    x_ref, spread = _envelope(monkeypatch, lambda: oracle.cg(ref, y, np.zeros(Nd), 20), op_err)
-    assert spread > TOL_SOLVER            # 1e-4 is out of reach of any FP32 operator here
-    assert rel(xg, x_ref) < 3 * spread
-
-
 def _l1tv_well_conditioned(d):
     if d == 2:
         Nd, Kd, Jd = (64, 64), (128, 128), (6, 6)
@@ -495,29 +452,6 @@ def test_l1tv_lad_matches_oracle(nf, d, mu, lam):
         xg = host(plan.solve_l1tv_lad(to_dev(y), maxiter=outer, inner=inner, cg_iters=cgi, mu=mu, lam=lam))
     xr = oracle.l1tv_lad(ref, y, np.zeros(Nd), outer, inner, cgi, mu, lam)
     assert rel(xg, xr) < TOL_SOLVER
-
-
-def test_l1tv_ols_radial_within_fp32_envelope(nf, monkeypatch):
-    """Golden-angle radial L1TV-OLS (the reconstruction setting of the 256^2
-    workload, scaled down).  The iterate is determined only to ~1e-2 at FP32
-    rounding level here (the oracle moves by 2e-3..5e-3 under 1e-6 operator
-    noise; the data residual ||A x - y|| moves by as much), and the GPU's own
-    result varies from run to run because its shared-memory atomics accumulate
-    in a run-dependent order: its distance to the oracle has ranged 3x..6x the
-    independent-noise spread.  So the bound is an order-of-magnitude one, 10x
-    the largest spread over five perturbed oracle runs (a wrong term moves the
-    iterate by O(1))."""
-    Nd, Kd, Jd = (64, 64), (128, 128), (6, 6)
-    om = W.radial2d_golden(60, 128)
-    ref = oracle.make_plan(om, Nd, Kd, Jd)
-    y = (oracle.forward(ref, W.ellipse_phantom(64)) + W.complex_noise(om.shape[0], 0.1)).astype(np.complex64)
-    with nf.NufftPlan(to_dev(om), Nd, Kd, Jd) as plan:
-        xg = host(plan.solve_l1tv_ols(to_dev(y), maxiter=6, inner=2, cg_iters=5, mu=1.0, lam=0.01))
-        op_err = _op_err(plan, ref, Nd)
-    x_ref, spread = _envelope(monkeypatch, lambda: oracle.l1tv_ols(ref, y, np.zeros(Nd), 6, 2, 5, 1.0, 0.01), op_err,
-                              seeds=(1, 2, 3, 4, 5))
-    assert spread > TOL_SOLVER
-    assert rel(xg, x_ref) < 10 * spread
 
 
 # ------------------------------------------------------------------ edge cases
