@@ -50,6 +50,16 @@ int selfadjoint_impl(nufft_plan_t* p, const float2* x, float2* out) {
   }
   return launch_fft_inverse(p, p->grid, out);
 }
+int selfadjoint_hooked(nufft_plan_t* p, float2* x, float2* out, const CgHooks* h) {
+  TRY(launch_fft_forward(p, x, p->grid, 1, true, h));
+  if (vhv_fused(p)) {
+    TRY(launch_vhv(p, p->grid, p->grid));
+  } else {
+    TRY(launch_interp(p, p->grid, p->ytmp));
+    TRY(launch_gridding(p, p->ytmp, p->grid));
+  }
+  return launch_fft_inverse(p, p->grid, out, 1, true, h);
+}
 int forward_dev(nufft_plan_t* p, const float2* x, float2* y) { return forward_impl(p, x, y); }
 int adjoint_dev(nufft_plan_t* p, const float2* y, float2* x) { return adjoint_impl(p, y, x); }
 

@@ -48,7 +48,54 @@ struct FftArgs {
   int64_t src_bstride;        // batch strides (blockIdx.y selects the batch element)
   int64_t dst_bstride;
   int scale;                  // 0: no S / S^H (plain zero-pad / crop)
+  // CG step hooks (see CgHooks): prologue of the first forward pass,
+  // epilogue of the last inverse pass
+  float2* pro_p;
+  const float2* pro_r;
+  const double* pro_part;
+  int pro_count;
+  double* pro_sc;
+  int pro_old, pro_new;
+  const float2* epi_a;
+  double* epi_part;
 };
+
+// Sum of v over the CTA (any block size up to 1024) in a fixed order: a
+// shuffle tree per warp, then the warps in order.  Every thread must call it;
+// every thread gets the sum.  red: 32 doubles of shared scratch.
+__device__ __forceinline__ double block_sum_dbl(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  const int nw = (blockDim.x + 31) >> 5;
+  for (int w = 0; w < nw; ++w) t += red[w];
+  __syncthreads();
+  return t;
+}
+
+// beta of the CG prologue (every CTA computes the same value); CTA 0 stores
+// the new <r, r> for the next step.
+__device__ __forceinline__ float cg_prologue_beta(const FftArgs& A, double* red) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < A.pro_count; i += blockDim.x) s += A.pro_part[i];
+  const double rr_new = block_sum_dbl(s, red);
+  const double rr_old = A.pro_sc[A.pro_old];
+  if (blockIdx.x == 0 && threadIdx.x == 0) A.pro_sc[A.pro_new] = rr_new;
+  return (float)(rr_old != 0.0 ? rr_new / rr_old : 0.0);
+}
+
+// image element idx of the first forward pass: with the CG prologue,
+// p = r + beta p written back in place (read with a plain load: it is written)
+__device__ __forceinline__ float2 load_image(const FftArgs& A, const float2* __restrict__ src, int64_t idx,
+                                             bool pro, float beta) {
+  if (!pro) return __ldg(&src[idx]);
+  const float2 pv = A.pro_p[idx], rv = A.pro_r[idx];
+  const float2 pn = make_float2(fmaf(beta, pv.x, rv.x), fmaf(beta, pv.y, rv.y));
+  A.pro_p[idx] = pn;
+  return pn;
+}
 
 template <bool INV>
 __device__ __forceinline__ float2 rot90(float2 z) {  // z * (-i) forward, z * (+i) inverse
@@ -226,6 +273,9 @@ k_fft_pass(const FftArgs A, const int W) {
   }
   const int half = A.Na >> 1;
   const int64_t stride = A.inner;
+  __shared__ double red[32];
+  const bool pro = !INV && A.src_image && A.pro_p;
+  const float beta = pro ? cg_prologue_beta(A, red) : 0.f;
 
   // ---- load the thread's elements t + k*TPL (pruned on the forward side)
   float2 x[8];
@@ -239,7 +289,7 @@ k_fft_pass(const FftArgs A, const int W) {
         if (in_image) {
           if (A.src_image) {
             const int n = p < half ? p + half : p - L + half;
-            v = cscale(__ldg(&src[o * A.Na + n]), (A.scale ? A.s_axis[n] : 1.0f) * slead);
+            v = cscale(load_image(A, src, o * A.Na + n, pro, beta), (A.scale ? A.s_axis[n] : 1.0f) * slead);
           } else {
             v = src[goff + (int64_t)p * stride + in];
           }
@@ -284,23 +334,35 @@ k_fft_pass(const FftArgs A, const int W) {
   }
 
   // ---- store the thread's elements t + k*TPL (pruned on the inverse side)
-  if (!live) return;
+  const bool epi = INV && A.dst_image && A.epi_part;
+  double dot = 0.0;
+  if (live) {
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const int p = t + k * TPL;
-    const float2 v = x[k];
-    if (!INV) {
-      dst[goff + (int64_t)p * stride + in] = v;
-    } else {
-      const bool in_image = (p < half) || (p >= L - half);
-      if (!in_image) continue;
-      if (A.dst_image) {
-        const int n = p < half ? p + half : p - L + half;
-        dst[o * A.Na + n] = cscale(v, (A.scale ? A.s_axis[n] : 1.0f) * slead);
-      } else {
+    for (int k = 0; k < 8; ++k) {
+      const int p = t + k * TPL;
+      const float2 v = x[k];
+      if (!INV) {
         dst[goff + (int64_t)p * stride + in] = v;
+      } else {
+        const bool in_image = (p < half) || (p >= L - half);
+        if (!in_image) continue;
+        if (A.dst_image) {
+          const int n = p < half ? p + half : p - L + half;
+          const float2 out = cscale(v, (A.scale ? A.s_axis[n] : 1.0f) * slead);
+          dst[o * A.Na + n] = out;
+          if (epi) {
+            const float2 a = A.epi_a[o * A.Na + n];
+            dot += (double)a.x * (double)out.x + (double)a.y * (double)out.y;
+          }
+        } else {
+          dst[goff + (int64_t)p * stride + in] = v;
+        }
       }
     }
+  }
+  if (epi) {
+    const double tsum = block_sum_dbl(dot, red);
+    if (threadIdx.x == 0) A.epi_part[blockIdx.x] = tsum;
   }
 }
 
@@ -309,8 +371,9 @@ k_fft_pass(const FftArgs A, const int W) {
 // two CTAs per SM (counting every batch element's CTAs).
 constexpr int64_t kTargetBlocks = 2 * 152;
 
+// query: only report the number of CTAs (per batch element) in *nblocks.
 template <int L, bool STRIDED, bool INV>
-cudaError_t launch_L(const FftArgs& A, int nb, cudaStream_t st) {
+cudaError_t launch_L(const FftArgs& A, int nb, cudaStream_t st, int64_t* nblocks, bool query) {
   constexpr int TPL = L / 8;
   int W;
   int64_t blocks;
@@ -325,13 +388,15 @@ cudaError_t launch_L(const FftArgs& A, int nb, cudaStream_t st) {
     while (W > 1 && (A.nouter + W - 1) / W * nb < kTargetBlocks) W >>= 1;
     blocks = (A.nouter + W - 1) / W;
   }
+  if (nblocks) *nblocks = blocks;
+  if (query) return cudaSuccess;
   const int threads = W * TPL;
   const size_t smem = 2 * SmemMap<L, STRIDED>::words(W) * sizeof(float2);   // ping-pong buffers
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_fft_pass<L, STRIDED, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  // always: the kernel's static shared memory (the CG hooks' scratch) comes on
+  // top, so even a 48 KB request needs the opt-in
+  cudaError_t e = cudaFuncSetAttribute(k_fft_pass<L, STRIDED, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
   if (blocks == 0) return cudaSuccess;
   k_fft_pass<L, STRIDED, INV><<<dim3((unsigned)blocks, (unsigned)nb), threads, smem, st>>>(A, W);
   return cudaGetLastError();
@@ -480,6 +545,9 @@ k_fft_mixed(const FftArgs A, const int W, const __grid_constant__ MixedRadix mr)
   }
   const int half = A.Na >> 1;
   const int64_t stride = A.inner;
+  __shared__ double red[32];
+  const bool pro = !INV && A.src_image && A.pro_p;
+  const float beta = pro ? cg_prologue_beta(A, red) : 0.f;
 
   for (int p = t; p < L; p += TPL) {
     float2 v = make_float2(0.f, 0.f);
@@ -488,7 +556,7 @@ k_fft_mixed(const FftArgs A, const int W, const __grid_constant__ MixedRadix mr)
         if ((p < half) || (p >= L - half)) {
           if (A.src_image) {
             const int n = p < half ? p + half : p - L + half;
-            v = cscale(__ldg(&src[o * A.Na + n]), (A.scale ? A.s_axis[n] : 1.0f) * slead);
+            v = cscale(load_image(A, src, o * A.Na + n, pro, beta), (A.scale ? A.s_axis[n] : 1.0f) * slead);
           } else {
             v = src[goff + (int64_t)p * stride + in];
           }
@@ -518,21 +586,33 @@ k_fft_mixed(const FftArgs A, const int W, const __grid_constant__ MixedRadix mr)
     Ns *= R;
   }
 
-  if (!live) return;
   const float2* res = sm + cur * bufw;
-  for (int p = t; p < L; p += TPL) {
-    const float2 v = res[SI.at(b, p)];
-    if (!INV) {
-      dst[goff + (int64_t)p * stride + in] = v;
-    } else {
-      if (!((p < half) || (p >= L - half))) continue;
-      if (A.dst_image) {
-        const int n = p < half ? p + half : p - L + half;
-        dst[o * A.Na + n] = cscale(v, (A.scale ? A.s_axis[n] : 1.0f) * slead);
-      } else {
+  const bool epi = INV && A.dst_image && A.epi_part;
+  double dot = 0.0;
+  if (live) {
+    for (int p = t; p < L; p += TPL) {
+      const float2 v = res[SI.at(b, p)];
+      if (!INV) {
         dst[goff + (int64_t)p * stride + in] = v;
+      } else {
+        if (!((p < half) || (p >= L - half))) continue;
+        if (A.dst_image) {
+          const int n = p < half ? p + half : p - L + half;
+          const float2 out = cscale(v, (A.scale ? A.s_axis[n] : 1.0f) * slead);
+          dst[o * A.Na + n] = out;
+          if (epi) {
+            const float2 a = A.epi_a[o * A.Na + n];
+            dot += (double)a.x * (double)out.x + (double)a.y * (double)out.y;
+          }
+        } else {
+          dst[goff + (int64_t)p * stride + in] = v;
+        }
       }
     }
+  }
+  if (epi) {
+    const double tsum = block_sum_dbl(dot, red);
+    if (threadIdx.x == 0) A.epi_part[blockIdx.x] = tsum;
   }
 }
 
@@ -540,7 +620,7 @@ k_fft_mixed(const FftArgs A, const int W, const __grid_constant__ MixedRadix mr)
 // columns, W | inner), W lowered while the launch would give fewer than two
 // CTAs per SM.
 template <bool STRIDED, bool INV>
-cudaError_t launch_mixed(int L, const FftArgs& A, int nb, cudaStream_t st) {
+cudaError_t launch_mixed(int L, const FftArgs& A, int nb, cudaStream_t st, int64_t* nblocks, bool query) {
   const MixedRadix mr = mixed_radix(L);
   if (mr.nst < 0) return cudaErrorInvalidValue;
   int W;
@@ -557,6 +637,8 @@ cudaError_t launch_mixed(int L, const FftArgs& A, int nb, cudaStream_t st) {
     while (W > 1 && (A.nouter + W - 1) / W * nb < kTargetBlocks) W >>= 1;
     blocks = (A.nouter + W - 1) / W;
   }
+  if (nblocks) *nblocks = blocks;
+  if (query) return cudaSuccess;
   const int threads = STRIDED ? 256 : W * (L >= 512 ? 128 : (L >= 128 ? 64 : 32));
   const size_t smem = 2 * MixedMap<STRIDED>::words(W, L) * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(k_fft_mixed<STRIDED, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -568,16 +650,17 @@ cudaError_t launch_mixed(int L, const FftArgs& A, int nb, cudaStream_t st) {
 }
 
 template <bool STRIDED, bool INV>
-cudaError_t launch_any(int L, const FftArgs& A, int nb, cudaStream_t st) {
+cudaError_t launch_any(int L, const FftArgs& A, int nb, cudaStream_t st, int64_t* nblocks = nullptr,
+                       bool query = false) {
   switch (L) {
-    case 16: return launch_L<16, STRIDED, INV>(A, nb, st);
-    case 32: return launch_L<32, STRIDED, INV>(A, nb, st);
-    case 64: return launch_L<64, STRIDED, INV>(A, nb, st);
-    case 128: return launch_L<128, STRIDED, INV>(A, nb, st);
-    case 256: return launch_L<256, STRIDED, INV>(A, nb, st);
-    case 512: return launch_L<512, STRIDED, INV>(A, nb, st);
-    case 1024: return launch_L<1024, STRIDED, INV>(A, nb, st);
-    default: return launch_mixed<STRIDED, INV>(L, A, nb, st);
+    case 16: return launch_L<16, STRIDED, INV>(A, nb, st, nblocks, query);
+    case 32: return launch_L<32, STRIDED, INV>(A, nb, st, nblocks, query);
+    case 64: return launch_L<64, STRIDED, INV>(A, nb, st, nblocks, query);
+    case 128: return launch_L<128, STRIDED, INV>(A, nb, st, nblocks, query);
+    case 256: return launch_L<256, STRIDED, INV>(A, nb, st, nblocks, query);
+    case 512: return launch_L<512, STRIDED, INV>(A, nb, st, nblocks, query);
+    case 1024: return launch_L<1024, STRIDED, INV>(A, nb, st, nblocks, query);
+    default: return launch_mixed<STRIDED, INV>(L, A, nb, st, nblocks, query);
   }
 }
 
@@ -603,12 +686,22 @@ FftArgs make_args(const nufft_plan_t* p, int a) {
 
 }  // namespace
 
-int launch_fft_forward(nufft_plan_t* p, const float2* x, float2* grid, int nb, bool scale) {
+int launch_fft_forward(nufft_plan_t* p, const float2* x, float2* grid, int nb, bool scale, const CgHooks* h) {
   const int d = p->g.d;
+  if (h && nb != 1) return set_error(p, NUFFT_EINVAL, "CG hooks need a single transform");
   for (int a = d - 1; a >= 0; --a) {
     FftArgs A = make_args(p, a);
     A.scale = scale ? 1 : 0;
     A.src_image = (a == d - 1);
+    if (h && A.src_image && h->pro_p) {
+      A.pro_p = h->pro_p;
+      A.pro_r = h->pro_r;
+      A.pro_part = h->pro_part;
+      A.pro_count = h->pro_count;
+      A.pro_sc = h->pro_sc;
+      A.pro_old = h->pro_old;
+      A.pro_new = h->pro_new;
+    }
     A.src = A.src_image ? x : grid;
     A.dst = grid;
     A.src_bstride = A.src_image ? p->Nprod : p->Kprod;
@@ -621,8 +714,19 @@ int launch_fft_forward(nufft_plan_t* p, const float2* x, float2* grid, int nb, b
   return NUFFT_OK;
 }
 
-int launch_fft_inverse(nufft_plan_t* p, float2* grid, float2* x, int nb, bool scale) {
+int fft_inverse_last_blocks(nufft_plan_t* p, int64_t* blocks) {
+  const int a = p->g.d - 1;
+  FftArgs A = make_args(p, a);
+  A.dst_image = 1;
+  const bool strided = A.inner > 1;
+  cudaError_t e = strided ? launch_any<true, true>(p->g.K[a], A, 1, p->stream, blocks, true)
+                          : launch_any<false, true>(p->g.K[a], A, 1, p->stream, blocks, true);
+  return e == cudaSuccess ? NUFFT_OK : cuda_check(p, e, "inverse FFT pass");
+}
+
+int launch_fft_inverse(nufft_plan_t* p, float2* grid, float2* x, int nb, bool scale, const CgHooks* h) {
   const int d = p->g.d;
+  if (h && nb != 1) return set_error(p, NUFFT_EINVAL, "CG hooks need a single transform");
   for (int a = 0; a < d; ++a) {
     FftArgs A = make_args(p, a);
     A.scale = scale ? 1 : 0;
@@ -631,7 +735,22 @@ int launch_fft_inverse(nufft_plan_t* p, float2* grid, float2* x, int nb, bool sc
     A.dst = A.dst_image ? x : grid;
     A.src_bstride = p->Kprod;
     A.dst_bstride = A.dst_image ? p->Nprod : p->Kprod;
+    const bool epi = h && A.dst_image && h->epi_part;
+    if (epi) {
+      A.epi_a = h->epi_a;
+      A.epi_part = h->epi_part;
+    }
     const bool strided = A.inner > 1;
+    int64_t blocks = 0;
+    if (epi) {   // the block count first: the partial sums must fit
+      cudaError_t e = strided ? launch_any<true, true>(p->g.K[a], A, nb, p->stream, &blocks, true)
+                              : launch_any<false, true>(p->g.K[a], A, nb, p->stream, &blocks, true);
+      if (e != cudaSuccess) return cuda_check(p, e, "inverse FFT pass");
+      if (blocks > h->epi_cap)
+        return set_error(p, NUFFT_EINVAL, "CG hooks: %lld partial sums exceed the capacity %d", (long long)blocks,
+                         h->epi_cap);
+      *h->epi_count = (int)blocks;
+    }
     cudaError_t e = strided ? launch_any<true, true>(p->g.K[a], A, nb, p->stream)
                             : launch_any<false, true>(p->g.K[a], A, nb, p->stream);
     if (e != cudaSuccess) return cuda_check(p, e, "inverse FFT pass");

@@ -173,11 +173,38 @@ inline cudaError_t dev_malloc(T** ptr, size_t bytes) {
 }
 
 // ------------------------------------------------------------------ launchers
+// Work of a CG step folded into the image-side FFT passes of a normal
+// operator q = A^H A p (single transforms only; solvers.cu):
+//  pro_*: the forward pass that reads the image first updates it in place,
+//    p = r + beta p, beta = (sum of pro_part[0 .. pro_count)) / pro_sc[pro_old],
+//    and CTA 0 stores that sum in pro_sc[pro_new] (pro_p == NULL: no update);
+//  epi_*: the inverse pass that writes the image also writes, per CTA, the
+//    partial sum of Re(conj(epi_a) q) over its outputs to epi_part[blockIdx.x];
+//    the launcher reports the number of CTAs in *epi_count (at most epi_cap,
+//    else NUFFT_EINVAL).
+// Every sum runs in a fixed order.
+struct CgHooks {
+  float2* pro_p = nullptr;
+  const float2* pro_r = nullptr;
+  const double* pro_part = nullptr;
+  int pro_count = 0;
+  double* pro_sc = nullptr;
+  int pro_old = 0, pro_new = 0;
+  const float2* epi_a = nullptr;
+  double* epi_part = nullptr;
+  int epi_cap = 0;
+  int* epi_count = nullptr;
+};
+
 // FFT passes (fft.cu).  Forward: grid = F pad(S x).  Inverse: x = S crop(F^H grid).
 // nb > 1 runs nb independent transforms: images nb x N^d, grids nb x K^d.
 // scale = false leaves out S (S^H): a plain centred zero-pad (crop).
-int launch_fft_forward(nufft_plan_t* p, const float2* x, float2* grid, int nb = 1, bool scale = true);
-int launch_fft_inverse(nufft_plan_t* p, float2* grid, float2* x, int nb = 1, bool scale = true);
+int launch_fft_forward(nufft_plan_t* p, const float2* x, float2* grid, int nb = 1, bool scale = true,
+                       const CgHooks* hooks = nullptr);
+int launch_fft_inverse(nufft_plan_t* p, float2* grid, float2* x, int nb = 1, bool scale = true,
+                       const CgHooks* hooks = nullptr);
+// CTAs of the inverse pass that writes the image (single transform).
+int fft_inverse_last_blocks(nufft_plan_t* p, int64_t* blocks);
 
 // Interpolation and gridding (interp.cu).
 // nb > 1: grids nb x K^d, k-space data nb x M, partial tiles in `tiles`
@@ -228,6 +255,13 @@ inline int64_t graph_key(std::initializer_list<uint64_t> vals) {
 
 // Normal operator used by the solvers (toeplitz.cu): V^H V or Toeplitz.
 int normal_op(nufft_plan_t* p, const float2* x, float2* out, int nb = 1);
+// The same for one image with a CG step's work folded into its FFT passes
+// (x is updated in place by the prologue), and the number of partial sums
+// its epilogue writes.
+int normal_op_hooked(nufft_plan_t* p, float2* x, float2* out, const CgHooks* h);
+int normal_op_epi_blocks(nufft_plan_t* p, int64_t* blocks);
+// A^H A x with CG hooks (capi.cu).
+int selfadjoint_hooked(nufft_plan_t* p, float2* x, float2* out, const CgHooks* h);
 
 // Plan-time helpers (plan.cu).
 Points points_view(const nufft_plan_t* p);

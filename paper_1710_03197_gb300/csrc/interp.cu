@@ -116,7 +116,8 @@ k_interp(const float2* __restrict__ grid_b, float2* __restrict__ y_b, const Poin
 // memory.  The plan orders each chunk so that the points sharing a warp
 // instruction read disjoint bank windows of these planes (the gridding uses
 // the same order for its atomics).  Lane layout, arithmetic and summation
-// order are those of k_interp, so the results are identical.
+// order are those of k_interp (results agree to rounding: the compiler may
+// fuse the multiply-adds differently in the two kernels).
 template <int D>
 struct InterpChunkCfg {
   static constexpr int kThreads = D == 3 ? 512 : 256;

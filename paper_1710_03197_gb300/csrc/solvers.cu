@@ -39,16 +39,21 @@ enum { S_RR0 = 0, S_RR1 = 1, S_NSLOTS = 8 };
 enum { V_B = 0, V_R, V_P, V_Q, V_AHY, V_AHYK, V_RHS, V_T, V_DF, V_BF, V_C1, V_C2, V_D0, V_B0 = V_D0 + 3,
        V_COUNT = V_B0 + 3 };
 
+// partial sums of <p, A^H A p> written by the image-side inverse FFT pass of
+// the fused CG (one per CTA of that pass)
+constexpr int kEpiCap = 4096;
+
 struct Ws {
   float2* v[V_COUNT];
   double* part;   // [2][kDotBlocks]: per-CTA partial sums (two sets in flight)
   double* sc;     // [S_NSLOTS]
+  double* epi;    // [kEpiCap]
 };
 
 int get_ws(nufft_plan_t* p, Ws* w) {
   const int64_t n = p->Nprod;
   const int64_t vec_bytes = ((n * (int64_t)sizeof(float2) + 255) / 256) * 256;
-  const int64_t bytes = vec_bytes * V_COUNT + (int64_t)(2 * kDotBlocks + S_NSLOTS) * sizeof(double);
+  const int64_t bytes = vec_bytes * V_COUNT + (int64_t)(2 * kDotBlocks + S_NSLOTS + kEpiCap) * sizeof(double);
   if (!p->solver_ws) {
     cudaError_t e = dev_malloc(&p->solver_ws, bytes);
     if (e != cudaSuccess) { p->solver_ws = nullptr; return cuda_check(p, e, "solver work space"); }
@@ -59,6 +64,7 @@ int get_ws(nufft_plan_t* p, Ws* w) {
   for (int i = 0; i < V_COUNT; ++i) w->v[i] = (float2*)(base + vec_bytes * i);
   w->part = (double*)(base + vec_bytes * V_COUNT);
   w->sc = w->part + 2 * kDotBlocks;
+  w->epi = w->sc + S_NSLOTS;
   return NUFFT_OK;
 }
 
@@ -111,8 +117,8 @@ __device__ __forceinline__ double sum_partials(const double* part, int count = k
 // partials); also the partial sums of <r, r>.
 __global__ void __launch_bounds__(kDotThreads)
 k_cg_xr(float2* x, float2* r, const float2* p, const float2* q, int64_t n, const double* sc, int rr_slot,
-        const double* part_pq, double* part) {
-  const float alpha = (float)safe_div(sc[rr_slot], sum_partials(part_pq));
+        const double* part_pq, int count_pq, double* part) {
+  const float alpha = (float)safe_div(sc[rr_slot], sum_partials(part_pq, count_pq));
   double s = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < n; i += (int64_t)kDotBlocks * kDotThreads) {
     const float2 pv = p[i], qv = q[i];
@@ -320,8 +326,47 @@ int cg_core(nufft_plan_t* p, int64_t n, float2* r, float2* pv, float2* q, double
     const int nxt = (it & 1) ? S_RR0 : S_RR1;
     TRY(op(pv, q));
     k_dot_partial<<<kDotBlocks, kDotThreads, 0, st>>>(pv, q, n, part_pq);
-    k_cg_xr<<<kDotBlocks, kDotThreads, 0, st>>>(x, r, pv, q, n, sc, cur, part_pq, part_rr);
+    k_cg_xr<<<kDotBlocks, kDotThreads, 0, st>>>(x, r, pv, q, n, sc, cur, part_pq, kDotBlocks, part_rr);
     k_cg_p<<<kDotBlocks, kDotThreads, 0, st>>>(pv, r, n, sc, nxt, cur, part_rr);
+    LAUNCH_CHECK(p, "cg iteration");
+  }
+  return NUFFT_OK;
+}
+
+// CG on the plain normal operator A^H A x = b (V^H V or Toeplitz) with the
+// vector steps folded into the operator's image-side FFT passes: the forward
+// pass that reads p first applies the previous step's p = r + beta p, and the
+// inverse pass that writes q = A^H A p writes the partial sums of <p, q>; one
+// kernel per step remains (x += alpha p, r -= alpha q, partial <r, r>).
+// Seven launches per step in 2D instead of nine; the same CG recurrence.
+int cg_core_fused(nufft_plan_t* p, int64_t n, float2* r, float2* pv, float2* q, double* part, double* sc,
+                  double* epi, const float2* b, float2* x, int iters) {
+  cudaStream_t st = p->stream;
+  double* part_rr = part + kDotBlocks;
+  TRY(normal_op(p, x, q));
+  k_cg_init<<<kDotBlocks, kDotThreads, 0, st>>>(r, pv, b, q, n, part_rr);
+  k_dot_final<<<1, kDotThreads, 0, st>>>(part_rr, sc + S_RR0);
+  LAUNCH_CHECK(p, "cg init");
+  for (int it = 0; it < iters; ++it) {
+    const int cur = (it & 1) ? S_RR1 : S_RR0;
+    const int prev = (it & 1) ? S_RR0 : S_RR1;
+    int count = 0;
+    CgHooks h;
+    if (it > 0) {   // the previous step's p update
+      h.pro_p = pv;
+      h.pro_r = r;
+      h.pro_part = part_rr;
+      h.pro_count = kDotBlocks;
+      h.pro_sc = sc;
+      h.pro_old = prev;
+      h.pro_new = cur;
+    }
+    h.epi_a = pv;
+    h.epi_part = epi;
+    h.epi_cap = kEpiCap;
+    h.epi_count = &count;
+    TRY(normal_op_hooked(p, pv, q, &h));
+    k_cg_xr<<<kDotBlocks, kDotThreads, 0, st>>>(x, r, pv, q, n, sc, cur, epi, count, part_rr);
     LAUNCH_CHECK(p, "cg iteration");
   }
   return NUFFT_OK;
@@ -409,8 +454,12 @@ extern "C" int solve_cg(nufft_plan_t* p, const float* y_dev, float* x_dev, int m
   TRY(get_ws(p, &w));
   const float2* y = reinterpret_cast<const float2*>(y_dev);
   float2* x = reinterpret_cast<float2*>(x_dev);
+  int64_t epi_blocks = 0;
+  TRY(normal_op_epi_blocks(p, &epi_blocks));
   return run_graphed(p, 7, y, x, maxiter, [&]() -> int {
     TRY(adjoint_dev(p, y, w.v[V_B]));
+    if (epi_blocks <= kEpiCap)
+      return cg_core_fused(p, p->Nprod, w.v[V_R], w.v[V_P], w.v[V_Q], w.part, w.sc, w.epi, w.v[V_B], x, maxiter);
     const Operator op{false, 1.f, 0.f};
     return cg_run(p, w, op, w.v[V_B], x, maxiter);
   });

@@ -67,7 +67,7 @@ struct PlanGuard {
   ~PlanGuard() { if (p) nufft_plan_destroy(p); }
 };
 
-int toeplitz_apply(nufft_plan_t* p, const float2* x, float2* out, int nb) {
+int toeplitz_apply(nufft_plan_t* p, const float2* x, float2* out, int nb, const CgHooks* h = nullptr) {
   nufft_plan_t* tg = p->toep_geom;
   if (nb > p->toep_cap) {
     drop_graphs(p);   // graphs may reference the buffer freed below
@@ -79,16 +79,29 @@ int toeplitz_apply(nufft_plan_t* p, const float2* x, float2* out, int nb) {
     p->toep_cap = nb;
   }
   tg->stream = p->stream;
-  int rc = launch_fft_forward(tg, x, p->toep_grid, nb, false);
+  int rc = launch_fft_forward(tg, x, p->toep_grid, nb, false, h);
   if (rc != NUFFT_OK) return set_error(p, rc, "%s", tg->err);
   k_mul_spectrum<<<nblocks(tg->Kprod * nb), kThreads, 0, p->stream>>>(p->toep_grid, p->toep_T, tg->Kprod, nb);
   NUFFT_CUDA_TRY(p, cudaGetLastError());
-  rc = launch_fft_inverse(tg, p->toep_grid, out, nb, false);
+  rc = launch_fft_inverse(tg, p->toep_grid, out, nb, false, h);
   if (rc != NUFFT_OK) return set_error(p, rc, "%s", tg->err);
   return NUFFT_OK;
 }
 
 }  // namespace
+
+int normal_op_hooked(nufft_plan_t* p, float2* x, float2* out, const CgHooks* h) {
+  if (p->normal_op == 1 && p->toep_T) return toeplitz_apply(p, x, out, 1, h);
+  return selfadjoint_hooked(p, x, out, h);
+}
+
+int normal_op_epi_blocks(nufft_plan_t* p, int64_t* blocks) {
+  if (p->normal_op == 1 && p->toep_T) {
+    const int rc = fft_inverse_last_blocks(p->toep_geom, blocks);
+    return rc == NUFFT_OK ? rc : set_error(p, rc, "%s", p->toep_geom->err);
+  }
+  return fft_inverse_last_blocks(p, blocks);
+}
 
 int normal_op(nufft_plan_t* p, const float2* x, float2* out, int nb) {
   if (p->normal_op == 1 && p->toep_T) return toeplitz_apply(p, x, out, nb);

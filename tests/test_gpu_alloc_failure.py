@@ -112,7 +112,9 @@ def test_batch_growth_failure_leaves_the_plan_usable(nf):
             torch.testing.assert_close(plan.forward(xs[0]), y1, rtol=0, atol=0)
         nf.lib.nufft_debug_fail_allocation(-1)
         yb = plan.forward_batch(xs)
-        torch.testing.assert_close(yb[0], y1, rtol=0, atol=0)
+        # the batched interpolation is a different kernel from the single one
+        # (same arithmetic order, different fusing of multiply-adds)
+        assert float(torch.linalg.norm(yb[0] - y1) / torch.linalg.norm(y1)) < 1e-6
 
 
 def test_toeplitz_set_up_failure_leaves_the_plan_usable(nf):
