@@ -30,6 +30,10 @@
  * - Every call returns a status; on failure nufft_last_error() describes it.
  * - A plan is not thread-safe: do not call into one plan from two host
  *   threads at once.  Distinct plans are independent.
+ * - Results are bit-identical from run to run for the same plan, inputs and
+ *   call: the gridding V^H accumulates each chunk of points in fixed point
+ *   (integer atomics under a per-chunk power-of-two scale), and every sum
+ *   across threads (tile reduction, solver inner products) has a fixed order.
  * - CUDA graphs: nufft_forward, nufft_adjoint, nufft_selfadjoint, their
  *   host-buffer forms (copies included when both host buffers are
  *   page-locked; other host memory runs eagerly), the stage calls, the batch and

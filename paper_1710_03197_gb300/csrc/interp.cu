@@ -230,6 +230,109 @@ k_interp_chunk(const float2* __restrict__ grid_b, float2* __restrict__ y_b, cons
   }
 }
 
+// 3D, J = 6, 16^3 tiles: as k_interp_chunk, and the point data are staged too,
+// kSub points at a time (two threads per point: first neighbours, the 18
+// coefficients, the permutation), so every global load of point data is a
+// coalesced row of consecutive points and the gathers read only shared
+// memory.  kSub = 160 points fill two rounds of the 16 warps' lane groups and
+// keep two CTAs per SM (74 KB tile + 25 KB point data each).
+constexpr int kSub3 = 160;
+__global__ void __launch_bounds__(512, 2)
+k_interp_chunk3d(const float2* __restrict__ grid_b, float2* __restrict__ y_b, const Chunk* __restrict__ chunks,
+                 const Points P, const Geom g, int64_t gbs, int64_t ybs) {
+  constexpr int JF = 6, PF = 21, ncell = PF * PF * PF;
+  extern __shared__ float tile[];
+  const float2* __restrict__ grid = grid_b + (int64_t)blockIdx.y * gbs;
+  float2* __restrict__ y = y_b + (int64_t)blockIdx.y * ybs;
+  float* gre = tile;
+  float* gim = tile + ncell;
+  float2* s_c0 = reinterpret_cast<float2*>(tile + 2 * ncell);   // [JF][kSub3] (2 * ncell floats: 8-byte aligned)
+  float2* s_c1 = s_c0 + JF * kSub3;                              // [JF][kSub3]
+  float2* s_c2 = s_c1 + JF * kSub3;                              // [kSub3][JF]
+  int* s_k = reinterpret_cast<int*>(s_c2 + JF * kSub3);          // [3][kSub3]
+  int* s_p = s_k + 3 * kSub3;                                    // [kSub3]
+  const Chunk ch = chunks[blockIdx.x];
+  int org[3];
+  {
+    int rem = ch.bin;
+    for (int a = 2; a >= 0; --a) {
+      org[a] = (rem % g.nb[a]) * 16;
+      rem /= g.nb[a];
+    }
+  }
+  for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+    const int r2 = c % PF, r1 = (c / PF) % PF, r0 = c / (PF * PF);
+    const int64_t gi = (int64_t)wrapk(org[0] + r0, g.K[0]) * g.Kstride[0] +
+                       (int64_t)wrapk(org[1] + r1, g.K[1]) * g.Kstride[1] + wrapk(org[2] + r2, g.K[2]);
+    const float2 v = __ldg(&grid[gi]);
+    gre[c] = v.x;
+    gim[c] = v.y;
+  }
+  const int lane = threadIdx.x & 31;
+  const int per_warp = 32 / JF;
+  const int sub = lane / JF;
+  const int l = lane - sub * JF;
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  for (int s0 = 0; s0 < ch.count; s0 += kSub3) {
+    const int cnt = min(kSub3, ch.count - s0);
+    __syncthreads();   // the tile is staged; the previous sub-chunk's data are consumed
+    {
+      // two threads per point: half 0 loads c0 and the first neighbours, half 1 c1, c2 and the permutation
+      const int q = threadIdx.x % kSub3, half = threadIdx.x / kSub3;
+      if (half < 2 && q < cnt) {
+        const int64_t i = (int64_t)ch.start + s0 + q;
+        if (half == 0) {
+#pragma unroll
+          for (int r = 0; r < JF; ++r) s_c0[r * kSub3 + q] = P.coef[P.coef_off[0] + (int64_t)r * P.M + i];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) s_k[a * kSub3 + q] = P.kf[(int64_t)a * P.M + i] - org[a];
+        } else {
+#pragma unroll
+          for (int r = 0; r < JF; ++r) s_c1[r * kSub3 + q] = P.coef[P.coef_off[1] + (int64_t)r * P.M + i];
+#pragma unroll
+          for (int r = 0; r < JF; ++r) s_c2[q * JF + r] = P.coef[P.coef_off[2] + (int64_t)r * P.M + i];
+          s_p[q] = P.perm[i];
+        }
+      }
+    }
+    __syncthreads();
+    for (int qb = warp * per_warp; qb < cnt; qb += nwarps * per_warp) {
+      const int q = qb + sub;
+      const bool act = (sub < per_warp) && (q < cnt);
+      float2 part = make_float2(0.f, 0.f);
+      if (act) {
+        const int ll = s_k[2 * kSub3 + q] + l;
+        const int l0 = s_k[q], l1 = s_k[kSub3 + q];
+        float2 c1v[JF];
+#pragma unroll
+        for (int j1 = 0; j1 < JF; ++j1) c1v[j1] = s_c1[j1 * kSub3 + q];
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j0 = 0; j0 < JF; ++j0) {
+          const int rowbase = ((l0 + j0) * PF + l1) * PF + ll;
+          float2 acc1 = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int j1 = 0; j1 < JF; ++j1) {
+            const int cell = rowbase + j1 * PF;
+            acc1 = cadd(acc1, cmul(c1v[j1], make_float2(gre[cell], gim[cell])));
+          }
+          acc = cadd(acc, cmul(s_c0[j0 * kSub3 + q], acc1));
+        }
+        part = cmul(s_c2[q * JF + l], acc);
+      }
+      const int base = sub * JF;
+      float2 tot = make_float2(0.f, 0.f);
+      for (int r = 0; r < JF; ++r) {
+        const int src = (base + r) & 31;
+        tot.x += __shfl_sync(0xffffffffu, part.x, src);
+        tot.y += __shfl_sync(0xffffffffu, part.y, src);
+      }
+      if (act && l == 0) y[s_p[q]] = tot;
+    }
+  }
+}
+
 // 2D: the chunk's point data are staged too (one thread per point: first
 // neighbours, the J0 + J1 coefficients and the permutation), so the CTA waits
 // for one round of global loads instead of one per pass of its warps over the
@@ -543,7 +646,7 @@ k_gridding_chunk(const float2* __restrict__ y_b, float2* __restrict__ tiles_b, c
 // for tiles written by other CTAs of the same launch.
 // The cells reduced are cbase .. cbase + (blockDim/NG)*CPT - 1 of the tile (all
 // of it when cbase = 0 and the groups span it).
-template <int D, int CPT, bool COHERENT>
+template <int D, int CPT, bool COHERENT, int TF>
 __device__ __forceinline__ void reduce_tile(const float2* __restrict__ tiles, const int32_t* __restrict__ bin_chunk,
                                             float2* __restrict__ grid, const Geom& g, const int NG, const int bin,
                                             float2* part, const int cbase = 0) {
@@ -574,13 +677,14 @@ __device__ __forceinline__ void reduce_tile(const float2* __restrict__ tiles, co
     s_delta[e] = delta;
   }
   __syncthreads();
-  const int T1 = D > 1 ? g.T[1] : 1, T2 = D > 2 ? g.T[2] : 1;
+  // TF > 0: every tile edge is TF, so the cell decompositions below divide by constants
+  const int T1 = D > 1 ? (TF > 0 ? TF : g.T[1]) : 1, T2 = D > 2 ? (TF > 0 ? TF : g.T[2]) : 1;
   int loc0[CPT];
   unsigned emask[CPT];
   int goff[CPT];
   float2 acc[CPT];
   int tile_cells = 1;
-  for (int a = 0; a < D; ++a) tile_cells *= g.T[a];
+  for (int a = 0; a < D; ++a) tile_cells *= TF > 0 ? TF : g.T[a];
   const int gsize = blockDim.x / NG;
   const int h = threadIdx.x / gsize;
   const int tg = threadIdx.x - h * gsize;
@@ -683,14 +787,14 @@ __device__ __forceinline__ void reduce_tile(const float2* __restrict__ tiles, co
 }
 
 // CTA x reduces slice x % slices of tile x / slices (slices of blockDim/NG*CPT cells).
-template <int D, int CPT>
+template <int D, int CPT, int TF>
 __global__ void __launch_bounds__(1024)
 k_gridding_reduce(const float2* __restrict__ tiles_b, const int32_t* __restrict__ bin_chunk,
                   float2* __restrict__ grid_b, const Geom g, const int NG, int64_t tbs, int64_t gbs, int slices) {
   extern __shared__ float2 part[];
   const int bin = blockIdx.x / slices;
   const int cbase = (blockIdx.x - bin * slices) * (blockDim.x / NG) * CPT;
-  reduce_tile<D, CPT, false>(tiles_b + (int64_t)blockIdx.y * tbs, bin_chunk, grid_b + (int64_t)blockIdx.y * gbs, g,
+  reduce_tile<D, CPT, false, TF>(tiles_b + (int64_t)blockIdx.y * tbs, bin_chunk, grid_b + (int64_t)blockIdx.y * gbs, g,
                              NG, bin, part, cbase);
 }
 
@@ -843,7 +947,10 @@ cudaError_t launch_reduce(const nufft_plan_t* p, const float2* tiles, float2* gr
   // runs one group per CTA so that more tiles are in flight per SM
   const int NG = (nb > 1 || slices > 1) ? 1 : std::max(1, std::min(4, 1024 / gsize));
   const size_t smem = NG > 1 ? (size_t)NG * 4 * gsize * sizeof(float2) : 0;
-  k_gridding_reduce<D, 4><<<dim3((unsigned)(p->g.nbins * slices), (unsigned)nb), gsize * NG, smem, p->stream>>>(
+  bool t16 = D > 1;
+  for (int a = 0; a < D; ++a) t16 = t16 && p->g.T[a] == 16;
+  auto kern = t16 ? k_gridding_reduce<D, 4, (D > 1 ? 16 : 0)> : k_gridding_reduce<D, 4, 0>;
+  kern<<<dim3((unsigned)(p->g.nbins * slices), (unsigned)nb), gsize * NG, smem, p->stream>>>(
       tiles, p->bin_chunk, grid, p->g, NG, p->nchunks * p->g.padded_cells, p->Kprod, slices);
   return cudaGetLastError();
 }
@@ -872,6 +979,14 @@ cudaError_t interp_chunks(const nufft_plan_t* p, const float2* grid, float2* y, 
     kern<<<gd, kChunkPoints[2], smem, p->stream>>>(grid, y, p->chunks, P, p->g, p->Kprod, p->M);
     return cudaGetLastError();
   } else {
+    if (j6 && t16) {
+      const size_t smem = (size_t)21 * 21 * 21 * 2 * sizeof(float) +
+                          (size_t)kSub3 * (3 * 6 * sizeof(float2) + 4 * sizeof(int));
+      cudaError_t e = cudaFuncSetAttribute(k_interp_chunk3d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k_interp_chunk3d<<<gd, 512, smem, p->stream>>>(grid, y, p->chunks, P, p->g, p->Kprod, p->M);
+      return cudaGetLastError();
+    }
     const size_t smem = (size_t)p->g.padded_cells * 2 * sizeof(float);
     auto kern = j6 ? (t16 ? k_interp_chunk<D, 6, 16> : k_interp_chunk<D, 6, 0>) : k_interp_chunk<D, 0, 0>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -182,8 +182,12 @@ __device__ __forceinline__ int64_t nb_index(const ImgGeom& G, int64_t i, int a, 
   return i + (c2 - c) * G.stride[a];
 }
 
-// out = mu q + lambda sum_a (2 p - p[-e_a] - p[+e_a])   (K applied to p; q = A^H A p)
-__global__ void k_tv_apply(float2* out, const float2* q, const float2* p, ImgGeom G, float mu, float lam) {
+// out = mu q + lambda sum_a (2 p - p[-e_a] - p[+e_a])   (K applied to p; q = A^H A p);
+// part != NULL: also the CTA's partial sum of Re(conj(p) out) in part[blockIdx.x]
+// (the CG step's <p, K p>; launched with kEwThreads == kDotThreads threads)
+__global__ void __launch_bounds__(kEwThreads)
+k_tv_apply(float2* out, const float2* q, const float2* p, ImgGeom G, float mu, float lam, double* part) {
+  double s = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < G.n; i += (int64_t)gridDim.x * blockDim.x) {
     const float2 pv = p[i];
     float2 lap = make_float2(0.f, 0.f);
@@ -193,7 +197,13 @@ __global__ void k_tv_apply(float2* out, const float2* q, const float2* p, ImgGeo
       lap.y += 2.f * pv.y - pm.y - pp.y;
     }
     const float2 qv = q[i];
-    out[i] = make_float2(mu * qv.x + lam * lap.x, mu * qv.y + lam * lap.y);
+    const float2 o = make_float2(mu * qv.x + lam * lap.x, mu * qv.y + lam * lap.y);
+    out[i] = o;
+    s += (double)pv.x * (double)o.x + (double)pv.y * (double)o.y;
+  }
+  if (part) {
+    const double t = block_sum(s);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
   }
 }
 
@@ -333,17 +343,33 @@ int cg_core(nufft_plan_t* p, int64_t n, float2* r, float2* pv, float2* q, double
   return NUFFT_OK;
 }
 
-// CG on the plain normal operator A^H A x = b (V^H V or Toeplitz) with the
-// vector steps folded into the operator's image-side FFT passes: the forward
-// pass that reads p first applies the previous step's p = r + beta p, and the
-// inverse pass that writes q = A^H A p writes the partial sums of <p, q>; one
-// kernel per step remains (x += alpha p, r -= alpha q, partial <r, r>).
-// Seven launches per step in 2D instead of nine; the same CG recurrence.
-int cg_core_fused(nufft_plan_t* p, int64_t n, float2* r, float2* pv, float2* q, double* part, double* sc,
-                  double* epi, const float2* b, float2* x, int iters) {
+struct Operator {
+  bool tv;       // false: A^H A; true: K = mu A^H A + lambda sum grad^T grad
+  float mu, lam;
+};
+
+int apply_op(nufft_plan_t* p, const Operator& op, const float2* in, float2* out, float2* tmp) {
+  if (!op.tv) return normal_op(p, in, out);
+  TRY(normal_op(p, in, tmp));
+  const ImgGeom G = img_geom(p);
+  k_tv_apply<<<ew_blocks(G.n), kEwThreads, 0, p->stream>>>(out, tmp, in, G, op.mu, op.lam, nullptr);
+  LAUNCH_CHECK(p, "tv apply");
+  return NUFFT_OK;
+}
+
+// CG with the vector steps folded into the operator's kernels (see CgHooks):
+// the forward FFT pass that reads p first applies the previous step's
+// p = r + beta p, and the kernel that writes q = op(p) writes one partial sum
+// of <p, q> per CTA (the image-side inverse FFT pass for A^H A, k_tv_apply for
+// K = mu A^H A + lambda sum grad^T grad); one kernel per step remains (alpha,
+// x += alpha p, r -= alpha q, partial <r, r>).  Seven launches per step for the
+// 2D normal operator instead of nine; the same CG recurrence.
+int cg_core_fused(nufft_plan_t* p, const Operator& op, int64_t n, float2* r, float2* pv, float2* q, float2* tmp,
+                  double* part, double* sc, double* epi, const float2* b, float2* x, int iters) {
   cudaStream_t st = p->stream;
   double* part_rr = part + kDotBlocks;
-  TRY(normal_op(p, x, q));
+  const ImgGeom G = img_geom(p);
+  TRY(apply_op(p, op, x, q, tmp));
   k_cg_init<<<kDotBlocks, kDotThreads, 0, st>>>(r, pv, b, q, n, part_rr);
   k_dot_final<<<1, kDotThreads, 0, st>>>(part_rr, sc + S_RR0);
   LAUNCH_CHECK(p, "cg init");
@@ -361,34 +387,35 @@ int cg_core_fused(nufft_plan_t* p, int64_t n, float2* r, float2* pv, float2* q, 
       h.pro_old = prev;
       h.pro_new = cur;
     }
-    h.epi_a = pv;
-    h.epi_part = epi;
-    h.epi_cap = kEpiCap;
-    h.epi_count = &count;
-    TRY(normal_op_hooked(p, pv, q, &h));
+    if (!op.tv) {
+      h.epi_a = pv;
+      h.epi_part = epi;
+      h.epi_cap = kEpiCap;
+      h.epi_count = &count;
+      TRY(normal_op_hooked(p, pv, q, &h));
+    } else {
+      TRY(normal_op_hooked(p, pv, tmp, &h));
+      count = ew_blocks(G.n);
+      k_tv_apply<<<count, kEwThreads, 0, st>>>(q, tmp, pv, G, op.mu, op.lam, epi);
+    }
     k_cg_xr<<<kDotBlocks, kDotThreads, 0, st>>>(x, r, pv, q, n, sc, cur, epi, count, part_rr);
     LAUNCH_CHECK(p, "cg iteration");
   }
   return NUFFT_OK;
 }
 
-struct Operator {
-  bool tv;       // false: A^H A; true: K = mu A^H A + lambda sum grad^T grad
-  float mu, lam;
-};
-
-int apply_op(nufft_plan_t* p, const Operator& op, const float2* in, float2* out, float2* tmp) {
-  if (!op.tv) return normal_op(p, in, out);
-  TRY(normal_op(p, in, tmp));
-  const ImgGeom G = img_geom(p);
-  k_tv_apply<<<ew_blocks(G.n), kEwThreads, 0, p->stream>>>(out, tmp, in, G, op.mu, op.lam);
-  LAUNCH_CHECK(p, "tv apply");
-  return NUFFT_OK;
-}
-
-// cg_iters CG steps on op x = b from the current x (in place), image-sized.
+// cg_iters CG steps on op x = b from the current x (in place), image-sized;
+// the fused steps whenever the operator's partial sums fit kEpiCap.
 int cg_run(nufft_plan_t* p, const Ws& w, const Operator& op, const float2* b, float2* x, int iters) {
   float2* t = w.v[V_T];
+  int64_t epi_blocks = 0;
+  if (op.tv) {
+    epi_blocks = ew_blocks(p->Nprod);
+  } else {
+    TRY(normal_op_epi_blocks(p, &epi_blocks));
+  }
+  if (epi_blocks <= kEpiCap)
+    return cg_core_fused(p, op, p->Nprod, w.v[V_R], w.v[V_P], w.v[V_Q], t, w.part, w.sc, w.epi, b, x, iters);
   return cg_core(p, p->Nprod, w.v[V_R], w.v[V_P], w.v[V_Q], w.part, w.sc,
                  [&](const float2* in, float2* out) { return apply_op(p, op, in, out, t); }, b, x, iters);
 }
@@ -454,12 +481,8 @@ extern "C" int solve_cg(nufft_plan_t* p, const float* y_dev, float* x_dev, int m
   TRY(get_ws(p, &w));
   const float2* y = reinterpret_cast<const float2*>(y_dev);
   float2* x = reinterpret_cast<float2*>(x_dev);
-  int64_t epi_blocks = 0;
-  TRY(normal_op_epi_blocks(p, &epi_blocks));
   return run_graphed(p, 7, y, x, maxiter, [&]() -> int {
     TRY(adjoint_dev(p, y, w.v[V_B]));
-    if (epi_blocks <= kEpiCap)
-      return cg_core_fused(p, p->Nprod, w.v[V_R], w.v[V_P], w.v[V_Q], w.part, w.sc, w.epi, w.v[V_B], x, maxiter);
     const Operator op{false, 1.f, 0.f};
     return cg_run(p, w, op, w.v[V_B], x, maxiter);
   });
