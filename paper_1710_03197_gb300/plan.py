@@ -20,6 +20,17 @@ def _stream_ptr(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+# torch's current stream as a raw handle without building a Stream object
+# (about 3 us per call less); torch.cuda.current_stream where it is missing
+_raw_current_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+
+
+def _current_stream_handle(device_index: int) -> int:
+    if _raw_current_stream is not None:
+        return int(_raw_current_stream(device_index))
+    return torch.cuda.current_stream(device_index).cuda_stream
+
+
 def _dev_ptr(t: torch.Tensor, numel: int, name: str, dtype=torch.complex64):
     if not isinstance(t, torch.Tensor):
         raise TypeError(f"{name} must be a torch.Tensor")
@@ -66,6 +77,7 @@ class NufftPlan:
         self.d, self.M = d, M
         self.Nd, self.Kd, self.Jd = tuple(int(v) for v in Nd), tuple(int(v) for v in Kd), tuple(int(v) for v in Jd)
         self.device = om.device
+        self._dev_index = om.device.index if om.device.index is not None else torch.cuda.current_device()
 
     # ---------------------------------------------------------------- lifetime
     @property
@@ -113,7 +125,7 @@ class NufftPlan:
     def _sync_stream(self):
         # order the plan's work on torch's current stream; the library keeps the
         # stream it was last given, so the call is skipped when it is unchanged
-        s = torch.cuda.current_stream().cuda_stream
+        s = _current_stream_handle(self._dev_index)
         if s != self._stream_key:
             check(lib.nufft_set_stream(self._h, ctypes.c_void_p(s)), self._h)
             self._stream_key = s
