@@ -283,6 +283,11 @@ __host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // conj(
 __host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) {
   return make_float2(a.x + b.x, a.y + b.y);
 }
+// acc + a * b as four fused multiply-adds (cadd(acc, cmul(a, b)) rounds the
+// product before the sum and takes six instructions)
+__host__ __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 acc) {
+  return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y)));
+}
 __host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) {
   return make_float2(a.x - b.x, a.y - b.y);
 }

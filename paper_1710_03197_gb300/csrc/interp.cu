@@ -62,7 +62,7 @@ k_interp(const float2* __restrict__ grid_b, float2* __restrict__ y_b, const Poin
         if (JF == 0 && j0 >= J0) break;
         const float2 c0 = P.coef[P.coef_off[0] + (int64_t)j0 * P.M + i];
         const int row = wrapk(k0 + j0, g.K[0]) * (int)g.Kstride[0];
-        acc = cadd(acc, cmul(c0, __ldg(&grid[row + gl])));
+        acc = cfma(c0, __ldg(&grid[row + gl]), acc);
       }
       part = cmul(cl, acc);
     } else {
@@ -90,9 +90,9 @@ k_interp(const float2* __restrict__ grid_b, float2* __restrict__ y_b, const Poin
 #pragma unroll
         for (int j1 = 0; j1 < (JF > 0 ? JF : kMaxJ); ++j1) {
           if (JF == 0 && j1 >= J1) break;
-          acc1 = cadd(acc1, cmul(c1v[j1], __ldg(&plane[rowoff[j1]])));
+          acc1 = cfma(c1v[j1], __ldg(&plane[rowoff[j1]]), acc1);
         }
-        acc = cadd(acc, cmul(c0, acc1));
+        acc = cfma(c0, acc1, acc);
       }
       part = cmul(cl, acc);
     }
@@ -192,7 +192,7 @@ k_interp_chunk(const float2* __restrict__ grid_b, float2* __restrict__ y_b, cons
           if (JF == 0 && j0 >= J0) break;
           const float2 c0 = P.coef[P.coef_off[0] + (int64_t)j0 * P.M + i];
           const int cell = (l0 + j0) * P1 + ll;
-          acc = cadd(acc, cmul(c0, make_float2(gre[cell], gim[cell])));
+          acc = cfma(c0, make_float2(gre[cell], gim[cell]), acc);
         }
       } else {
         const int l1 = P.kf[P.M + i] - org[1];
@@ -212,9 +212,9 @@ k_interp_chunk(const float2* __restrict__ grid_b, float2* __restrict__ y_b, cons
           for (int j1 = 0; j1 < (JF > 0 ? JF : kMaxJ); ++j1) {
             if (JF == 0 && j1 >= J1) break;
             const int cell = rowbase + j1 * P2;
-            acc1 = cadd(acc1, cmul(c1v[j1], make_float2(gre[cell], gim[cell])));
+            acc1 = cfma(c1v[j1], make_float2(gre[cell], gim[cell]), acc1);
           }
-          acc = cadd(acc, cmul(c0, acc1));
+          acc = cfma(c0, acc1, acc);
         }
       }
       part = cmul(cl, acc);
@@ -315,9 +315,9 @@ k_interp_chunk3d(const float2* __restrict__ grid_b, float2* __restrict__ y_b, co
 #pragma unroll
           for (int j1 = 0; j1 < JF; ++j1) {
             const int cell = rowbase + j1 * PF;
-            acc1 = cadd(acc1, cmul(c1v[j1], make_float2(gre[cell], gim[cell])));
+            acc1 = cfma(c1v[j1], make_float2(gre[cell], gim[cell]), acc1);
           }
-          acc = cadd(acc, cmul(s_c0[j0 * kSub3 + q], acc1));
+          acc = cfma(s_c0[j0 * kSub3 + q], acc1, acc);
         }
         part = cmul(s_c2[q * JF + l], acc);
       }
@@ -404,7 +404,7 @@ k_interp_chunk2d(const float2* __restrict__ grid_b, float2* __restrict__ y_b, co
       for (int j0 = 0; j0 < (JF > 0 ? JF : kMaxJ); ++j0) {
         if (JF == 0 && j0 >= J0) break;
         const int cell = (l0 + j0) * P1 + ll;
-        acc = cadd(acc, cmul(s_c[j0 * cap + q], make_float2(gre[cell], gim[cell])));
+        acc = cfma(s_c[j0 * cap + q], make_float2(gre[cell], gim[cell]), acc);
       }
       part = cmul(s_c[J0 * cap + q * J1 + l], acc);
     }
@@ -894,7 +894,7 @@ k_gridding_chunk_staged(const float2* __restrict__ y_b, float2* __restrict__ til
         for (int j0 = 0; j0 < (JF > 0 ? JF : kMaxJ); ++j0) {
           if (JF == 0 && j0 >= J0) break;
           const int cell = (l0 + j0) * P1 + ll;
-          a = cadd(a, cmul(s_c[j0 * cap + q], make_float2(gre[cell], gim[cell])));
+          a = cfma(s_c[j0 * cap + q], make_float2(gre[cell], gim[cell]), a);
         }
         part = cmul(s_c[J0 * cap + q * J1 + l], a);
       }
