@@ -276,6 +276,7 @@ k_fft_pass(const FftArgs A, const int W) {
   __shared__ double red[32];
   const bool pro = !INV && A.src_image && A.pro_p;
   const float beta = pro ? cg_prologue_beta(A, red) : 0.f;
+  const uint64_t pol = l2_evict_first_policy();   // a pass reads each input element once
 
   // ---- load the thread's elements t + k*TPL (pruned on the forward side)
   float2 x[8];
@@ -291,11 +292,11 @@ k_fft_pass(const FftArgs A, const int W) {
             const int n = p < half ? p + half : p - L + half;
             v = cscale(load_image(A, src, o * A.Na + n, pro, beta), (A.scale ? A.s_axis[n] : 1.0f) * slead);
           } else {
-            v = src[goff + (int64_t)p * stride + in];
+            v = ld_last_use(&src[goff + (int64_t)p * stride + in], pol);
           }
         }
       } else {
-        v = src[goff + (int64_t)p * stride + in];
+        v = ld_last_use(&src[goff + (int64_t)p * stride + in], pol);
       }
     }
     x[k] = v;
@@ -548,6 +549,7 @@ k_fft_mixed(const FftArgs A, const int W, const __grid_constant__ MixedRadix mr)
   __shared__ double red[32];
   const bool pro = !INV && A.src_image && A.pro_p;
   const float beta = pro ? cg_prologue_beta(A, red) : 0.f;
+  const uint64_t pol = l2_evict_first_policy();   // a pass reads each input element once
 
   for (int p = t; p < L; p += TPL) {
     float2 v = make_float2(0.f, 0.f);
@@ -558,11 +560,11 @@ k_fft_mixed(const FftArgs A, const int W, const __grid_constant__ MixedRadix mr)
             const int n = p < half ? p + half : p - L + half;
             v = cscale(load_image(A, src, o * A.Na + n, pro, beta), (A.scale ? A.s_axis[n] : 1.0f) * slead);
           } else {
-            v = src[goff + (int64_t)p * stride + in];
+            v = ld_last_use(&src[goff + (int64_t)p * stride + in], pol);
           }
         }
       } else {
-        v = src[goff + (int64_t)p * stride + in];
+        v = ld_last_use(&src[goff + (int64_t)p * stride + in], pol);
       }
     }
     sm[SI.at(b, p)] = v;

@@ -283,6 +283,21 @@ __host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // conj(
 __host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) {
   return make_float2(a.x + b.x, a.y + b.y);
 }
+// Loads of data read for the last time (a line pass's input), marked
+// evict-first in L2 so that they do not push out what the launch writes for
+// the next one (a 3D pass's 67 MB output stays in L2 while it streams the
+// 134 MB grid in).
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ float2 ld_last_use(const float2* ptr, uint64_t pol) {
+  float2 v;
+  asm volatile("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(ptr), "l"(pol));
+  return v;
+}
+
 // acc + a * b as four fused multiply-adds (cadd(acc, cmul(a, b)) rounds the
 // product before the sum and takes six instructions)
 __host__ __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 acc) {
