@@ -278,6 +278,16 @@ k_fft_pass(const FftArgs A, const int W) {
   const float beta = pro ? cg_prologue_beta(A, red) : 0.f;
   const uint64_t pol = l2_evict_first_policy();   // a pass reads each input element once
 
+  constexpr int LOG = ilog2(L);
+  constexpr int R0 = 1 << (LOG % 3);
+  constexpr int N8 = LOG / 3;
+  // Lines of 512 and more (2D grids: a few warps per SM) load each radix-8
+  // stage's twiddles one stage ahead, the first ones before the elements, so
+  // that no stage waits on a twiddle round trip to L2.
+  constexpr bool kAhead = L >= 512;
+  StageTw<L, 8> Tn;
+  if (kAhead) load_twiddles<L, INV, 8>(Tn, t, R0 == 1 ? 8 : R0, A.tw);
+
   // ---- load the thread's elements t + k*TPL (pruned on the forward side)
   float2 x[8];
 #pragma unroll
@@ -303,9 +313,6 @@ k_fft_pass(const FftArgs A, const int W) {
   }
 
   // ---- transform: an optional radix-2/4 stage, then radix-8 stages
-  constexpr int LOG = ilog2(L);
-  constexpr int R0 = 1 << (LOG % 3);
-  constexpr int N8 = LOG / 3;
   int Ns = 1;
   int cur = 0;
   if (R0 > 1) {
@@ -319,7 +326,12 @@ k_fft_pass(const FftArgs A, const int W) {
     StageTw<L, 8> T;
     const bool first = (R0 == 1 && s == 0);
     if (!first) {
-      load_twiddles<L, INV, 8>(T, t, Ns, A.tw);
+      if (kAhead) {
+        T = Tn;
+        if (s + 1 < N8) load_twiddles<L, INV, 8>(Tn, t, Ns * 8, A.tw);
+      } else {
+        load_twiddles<L, INV, 8>(T, t, Ns, A.tw);
+      }
       __syncthreads();
       read_own<L, STRIDED>(sm + cur * bufw, SI, b, t, x);
       butterflies<L, INV, 8, true>(x, T);
