@@ -646,6 +646,18 @@ k_gridding_chunk(const float2* __restrict__ y_b, float2* __restrict__ tiles_b, c
 // for tiles written by other CTAs of the same launch.
 // The cells reduced are cbase .. cbase + (blockDim/NG)*CPT - 1 of the tile (all
 // of it when cbase = 0 and the groups span it).
+// Entry n (2^D bits at bit 2^D * n) is the set of the e in [0, 2^D) with
+// e & ~n == 0: the neighbours whose padded tiles reach a cell that is near the
+// low edge of its tile along the axes in n.
+template <int D>
+__host__ __device__ constexpr uint64_t subset_masks() {
+  uint64_t t = 0;
+  for (unsigned n = 0; n < (1u << D); ++n)
+    for (unsigned e = 0; e < (1u << D); ++e)
+      if ((e & ~n) == 0) t |= uint64_t(1) << ((1u << D) * n + e);
+  return t;
+}
+
 template <int D, int CPT, bool COHERENT, int TF>
 __device__ __forceinline__ void reduce_tile(const float2* __restrict__ tiles, const int32_t* __restrict__ bin_chunk,
                                             float2* __restrict__ grid, const Geom& g, const int NG, const int bin,
@@ -711,15 +723,13 @@ __device__ __forceinline__ void reduce_tile(const float2* __restrict__ tiles, co
       lc[0] = c / (T2 * T1);
     }
     loc0[k] = D == 1 ? lc[0] : (D == 2 ? lc[0] * P1 + lc[1] : (lc[0] * P1 + lc[1]) * P2 + lc[2]);
-    unsigned m = 0;
+    // neighbour e reaches the cell iff every axis a with e_a = 1 has the cell
+    // within J - 1 of the tile's low edge; with those axes as the bits of
+    // `near` (e's bit order), the mask is the set of subsets of near
+    unsigned near = 0;
 #pragma unroll
-    for (int e = 0; e < (1 << D); ++e) {
-      bool ok = true;
-#pragma unroll
-      for (int a = 0; a < D; ++a)
-        if ((e >> (D - 1 - a)) & 1) ok = ok && (lc[a] + g.T[a] < g.P[a]);
-      m |= (ok ? 1u : 0u) << e;
-    }
+    for (int a = 0; a < D; ++a) near |= (lc[a] + g.T[a] < g.P[a] ? 1u : 0u) << (D - 1 - a);
+    const unsigned m = (unsigned)(subset_masks<D>() >> ((1 << D) * near)) & ((1u << (1 << D)) - 1u);
     emask[k] = (cbase + tg + k * gsize < cend) ? m : 0u;
     int off = 0;
 #pragma unroll
