@@ -29,6 +29,32 @@ namespace nufft {
 namespace {
 
 // ---------------------------------------------------------------- interpolation
+// Sum of `part` over the lanes base .. base + G - 1 of a lane group, valid in
+// lane base; every lane of the warp takes part.  Groups of 6 (J = 6) sum as
+// (p0 + p3) + (p1 + p4) + (p2 + p5) with three shuffle steps; other widths add
+// the lanes in order.
+template <int JF>
+__device__ __forceinline__ float2 lane_group_sum(float2 part, int base, int G) {
+  if constexpr (JF == 6) {
+    float2 a, s;
+    a.x = part.x + __shfl_down_sync(0xffffffffu, part.x, 3);
+    a.y = part.y + __shfl_down_sync(0xffffffffu, part.y, 3);
+    s.x = a.x + __shfl_down_sync(0xffffffffu, a.x, 1);
+    s.y = a.y + __shfl_down_sync(0xffffffffu, a.y, 1);
+    s.x += __shfl_down_sync(0xffffffffu, a.x, 2);
+    s.y += __shfl_down_sync(0xffffffffu, a.y, 2);
+    return s;
+  } else {
+    float2 tot = make_float2(0.f, 0.f);
+    for (int r = 0; r < G; ++r) {
+      const int src = (base + r) & 31;
+      tot.x += __shfl_sync(0xffffffffu, part.x, src);
+      tot.y += __shfl_sync(0xffffffffu, part.y, src);
+    }
+    return tot;
+  }
+}
+
 template <int D, int JF>
 __global__ void __launch_bounds__(256)
 k_interp(const float2* __restrict__ grid_b, float2* __restrict__ y_b, const Points P, const Geom g, int64_t gbs,
@@ -97,14 +123,8 @@ k_interp(const float2* __restrict__ grid_b, float2* __restrict__ y_b, const Poin
       part = cmul(cl, acc);
     }
   }
-  // Sum the G partial values of each lane group (fixed order: lane base .. base+G-1).
-  const int base = sub * G;
-  float2 tot = make_float2(0.f, 0.f);
-  for (int q = 0; q < G; ++q) {
-    const int src = (base + q) & 31;
-    tot.x += __shfl_sync(0xffffffffu, part.x, src);
-    tot.y += __shfl_sync(0xffffffffu, part.y, src);
-  }
+  // Sum the G partial values of each lane group (a fixed order).
+  const float2 tot = lane_group_sum<JF>(part, sub * G, G);
   if (active && l == 0) y[P.perm[i]] = tot;
 }
 
@@ -219,13 +239,7 @@ k_interp_chunk(const float2* __restrict__ grid_b, float2* __restrict__ y_b, cons
       }
       part = cmul(cl, acc);
     }
-    const int base = sub * G;
-    float2 tot = make_float2(0.f, 0.f);
-    for (int r = 0; r < G; ++r) {
-      const int src = (base + r) & 31;
-      tot.x += __shfl_sync(0xffffffffu, part.x, src);
-      tot.y += __shfl_sync(0xffffffffu, part.y, src);
-    }
+    const float2 tot = lane_group_sum<JF>(part, sub * G, G);
     if (act && l == 0) y[P.perm[i]] = tot;
   }
 }
@@ -321,13 +335,7 @@ k_interp_chunk3d(const float2* __restrict__ grid_b, float2* __restrict__ y_b, co
         }
         part = cmul(s_c2[q * JF + l], acc);
       }
-      const int base = sub * JF;
-      float2 tot = make_float2(0.f, 0.f);
-      for (int r = 0; r < JF; ++r) {
-        const int src = (base + r) & 31;
-        tot.x += __shfl_sync(0xffffffffu, part.x, src);
-        tot.y += __shfl_sync(0xffffffffu, part.y, src);
-      }
+      const float2 tot = lane_group_sum<6>(part, sub * JF, JF);
       if (act && l == 0) y[s_p[q]] = tot;
     }
   }
@@ -408,13 +416,7 @@ k_interp_chunk2d(const float2* __restrict__ grid_b, float2* __restrict__ y_b, co
       }
       part = cmul(s_c[J0 * cap + q * J1 + l], acc);
     }
-    const int base = sub * G;
-    float2 tot = make_float2(0.f, 0.f);
-    for (int r = 0; r < G; ++r) {
-      const int src = (base + r) & 31;
-      tot.x += __shfl_sync(0xffffffffu, part.x, src);
-      tot.y += __shfl_sync(0xffffffffu, part.y, src);
-    }
+    const float2 tot = lane_group_sum<JF>(part, sub * G, G);
     if (act && l == 0) y[s_p[q]] = tot;
   }
 }
@@ -908,13 +910,7 @@ k_gridding_chunk_staged(const float2* __restrict__ y_b, float2* __restrict__ til
         }
         part = cmul(s_c[J0 * cap + q * J1 + l], a);
       }
-      const int base = sub * G;
-      float2 yv = make_float2(0.f, 0.f);
-      for (int r = 0; r < G; ++r) {
-        const int src = (base + r) & 31;
-        yv.x += __shfl_sync(0xffffffffu, part.x, src);
-        yv.y += __shfl_sync(0xffffffffu, part.y, src);
-      }
+      const float2 yv = lane_group_sum<JF>(part, sub * G, G);
       if (act && l == 0) s_y[q] = yv;
     }
     __syncthreads();
