@@ -168,25 +168,31 @@ struct SmemMap {
 // (Ns = L/R, written to j + r*Ns) are again elements t + k*TPL, stored straight
 // to global memory.  Only the middle hand-offs go through shared memory.
 template <int L, int R>
-struct StageTw {                      // twiddles of one stage, loaded ahead of its barrier
+struct StageTw {                      // twiddles of one stage
   float2 w[8 / R][R];
 };
 
-template <int L, bool INV, int R>
-__device__ __forceinline__ void load_twiddles(StageTw<L, R>& T, int t, int Ns, const float2* __restrict__ tw) {
-  constexpr int TPL = L / 8;
-  constexpr int Q = 8 / R;
-  const int step = L / (Ns * R);
-#pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    const int k = (t + q * TPL) & (Ns - 1);
-#pragma unroll
-    for (int r = 1; r < R; ++r) {
-      float2 w = __ldg(&tw[r * k * step]);
-      if (INV) w.y = -w.y;
-      T.w[q][r] = w;
-    }
-  }
+// Twiddles of a radix-8 stage, computed: input r of the thread's butterfly
+// gets w1^r, w1 = exp(-+ 2 pi i k / (Ns R)), from sincospif (2k / (Ns R) is
+// exact: Ns R is a power of two) and products of depth at most three (a few
+// ulp; a table rounded from FP64 would be 0.5 ulp).  The passes then issue no
+// twiddle loads (the strided 3D passes are bound by the L1/shared pipe, the
+// 2D ones by load latency).
+template <int L, bool INV>
+__device__ __forceinline__ void make_twiddles8(StageTw<L, 8>& T, int t, int Ns) {
+  const float inv = 2.0f / (float)(Ns * 8);   // exact
+  const int k = t & (Ns - 1);                  // radix 8: one butterfly per thread
+  float sn, cs;
+  sincospif((float)k * inv, &sn, &cs);
+  const float2 w1 = make_float2(cs, INV ? sn : -sn);
+  const float2 w2 = cmul(w1, w1), w4 = cmul(w2, w2);
+  T.w[0][1] = w1;
+  T.w[0][2] = w2;
+  T.w[0][3] = cmul(w2, w1);
+  T.w[0][4] = w4;
+  T.w[0][5] = cmul(w4, w1);
+  T.w[0][6] = cmul(w4, w2);
+  T.w[0][7] = cmul(w4, T.w[0][3]);
 }
 
 template <int L, bool INV, int R, bool TW>
@@ -281,13 +287,6 @@ k_fft_pass(const FftArgs A, const int W) {
   constexpr int LOG = ilog2(L);
   constexpr int R0 = 1 << (LOG % 3);
   constexpr int N8 = LOG / 3;
-  // Lines of 512 and more (2D grids: a few warps per SM) load each radix-8
-  // stage's twiddles one stage ahead, the first ones before the elements, so
-  // that no stage waits on a twiddle round trip to L2.
-  constexpr bool kAhead = L >= 512;
-  StageTw<L, 8> Tn;
-  if (kAhead) load_twiddles<L, INV, 8>(Tn, t, R0 == 1 ? 8 : R0, A.tw);
-
   // ---- load the thread's elements t + k*TPL (pruned on the forward side)
   float2 x[8];
 #pragma unroll
@@ -326,12 +325,7 @@ k_fft_pass(const FftArgs A, const int W) {
     StageTw<L, 8> T;
     const bool first = (R0 == 1 && s == 0);
     if (!first) {
-      if (kAhead) {
-        T = Tn;
-        if (s + 1 < N8) load_twiddles<L, INV, 8>(Tn, t, Ns * 8, A.tw);
-      } else {
-        load_twiddles<L, INV, 8>(T, t, Ns, A.tw);
-      }
+      make_twiddles8<L, INV>(T, t, Ns);
       __syncthreads();
       read_own<L, STRIDED>(sm + cur * bufw, SI, b, t, x);
       butterflies<L, INV, 8, true>(x, T);
