@@ -491,15 +491,17 @@ __device__ __forceinline__ void fix_add(int* acc, int ncell, int cell, float2 w)
     atomicAdd(&acc[ncell + cell], __float2int_rn(w.y));
   } else {
     // x + 1.5 * 2^23 rounds x to an integer when |x| < 2^22, and the float's
-    // bits minus those of 1.5 * 2^23 are that integer.
+    // bits minus those of 1.5 * 2^23 are that integer (the high parts); the
+    // exact remainders are rounded by the conversion unit (the same
+    // round-to-nearest-even), one instruction each on an otherwise idle pipe.
     const float magic = 12582912.0f;
     const float hr = fmaf(w.x, 0x1p-20f, magic), hi_ = fmaf(w.y, 0x1p-20f, magic);
-    const float lr = fmaf(-(hr - magic), 0x1p20f, w.x) + magic;   // remainder (exact), rounded
-    const float li = fmaf(-(hi_ - magic), 0x1p20f, w.y) + magic;
+    const float lr = fmaf(-(hr - magic), 0x1p20f, w.x);   // remainder (exact)
+    const float li = fmaf(-(hi_ - magic), 0x1p20f, w.y);
     const int hre = __float_as_int(hr) - 0x4B400000, him = __float_as_int(hi_) - 0x4B400000;
     atomicAdd(&acc[cell], him * 65536 + hre);
-    atomicAdd(&acc[ncell + cell], __float_as_int(lr) - 0x4B400000);
-    atomicAdd(&acc[2 * ncell + cell], __float_as_int(li) - 0x4B400000);
+    atomicAdd(&acc[ncell + cell], __float2int_rn(lr));
+    atomicAdd(&acc[2 * ncell + cell], __float2int_rn(li));
   }
 }
 
