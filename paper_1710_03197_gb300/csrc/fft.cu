@@ -33,7 +33,6 @@ namespace {
 struct FftArgs {
   const float2* src;
   float2* dst;
-  const float2* tw;           // K_a forward twiddles
   const float* s_axis;        // scaling of axis a (image side only)
   const float* s_lead[kMaxDim];
   int a;
@@ -483,22 +482,24 @@ struct MixedMap {
 
 template <int R, bool INV, bool STRIDED>
 __device__ __forceinline__ void mixed_stage(const float2* __restrict__ src, float2* __restrict__ dst,
-                                            const MixedMap<STRIDED> SI, int b, int t, int TPL, int Ns,
-                                            const float2* __restrict__ tw) {
+                                            const MixedMap<STRIDED> SI, int b, int t, int TPL, int Ns) {
   const int L = SI.L;
   const int nbf = L / R;
-  const int step = L / (Ns * R);
+  const float inv = 2.0f / (float)(Ns * R);
   for (int j = t; j < nbf; j += TPL) {
     const int k = j % Ns;
     float2 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = src[SI.at(b, j + r * nbf)];
-    if (Ns > 1) {
+    if (Ns > 1) {   // input r times w1^r, w1 = exp(-+ 2 pi i k / (Ns R)), computed (no table loads)
+      float sn, cs;
+      sincospif((float)k * inv, &sn, &cs);
+      const float2 w1 = make_float2(cs, INV ? sn : -sn);
+      float2 w = w1;
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        float2 w = __ldg(&tw[r * k * step]);
-        if (INV) w.y = -w.y;
         v[r] = cmul(v[r], w);
+        if (r + 1 < R) w = cmul(w, w1);
       }
     }
     if (R == 3) dft3<INV>(v);
@@ -583,11 +584,11 @@ k_fft_mixed(const FftArgs A, const int W, const __grid_constant__ MixedRadix mr)
     const float2* in_buf = sm + cur * bufw;
     float2* out_buf = sm + (cur ^ 1) * bufw;
     switch (R) {
-      case 2: mixed_stage<2, INV>(in_buf, out_buf, SI, b, t, TPL, Ns, A.tw); break;
-      case 3: mixed_stage<3, INV>(in_buf, out_buf, SI, b, t, TPL, Ns, A.tw); break;
-      case 4: mixed_stage<4, INV>(in_buf, out_buf, SI, b, t, TPL, Ns, A.tw); break;
-      case 5: mixed_stage<5, INV>(in_buf, out_buf, SI, b, t, TPL, Ns, A.tw); break;
-      default: mixed_stage<8, INV>(in_buf, out_buf, SI, b, t, TPL, Ns, A.tw); break;
+      case 2: mixed_stage<2, INV>(in_buf, out_buf, SI, b, t, TPL, Ns); break;
+      case 3: mixed_stage<3, INV>(in_buf, out_buf, SI, b, t, TPL, Ns); break;
+      case 4: mixed_stage<4, INV>(in_buf, out_buf, SI, b, t, TPL, Ns); break;
+      case 5: mixed_stage<5, INV>(in_buf, out_buf, SI, b, t, TPL, Ns); break;
+      default: mixed_stage<8, INV>(in_buf, out_buf, SI, b, t, TPL, Ns); break;
     }
     __syncthreads();
     cur ^= 1;
@@ -678,7 +679,6 @@ FftArgs make_args(const nufft_plan_t* p, int a) {
   const Geom& g = p->g;
   A.a = a;
   A.Na = g.N[a];
-  A.tw = p->twiddle + p->tw_off[a];
   A.s_axis = p->s + p->s_off[a];
   A.nouter = 1;
   for (int i = 0; i < a; ++i) {

@@ -82,8 +82,6 @@ struct nufft_plan {
   // plan-owned device memory
   float* s;                 // scaling, dim i at s + s_off[i]
   int64_t s_off[nufft::kMaxDim];
-  float2* twiddle;          // forward twiddles exp(-2 pi i k / K_i), dim i at tw_off[i]
-  int64_t tw_off[nufft::kMaxDim];
   int32_t* kf;              // [d][M] sorted
   float2* coef;             // [sum_i J_i][M] sorted
   int64_t coef_off[nufft::kMaxDim];

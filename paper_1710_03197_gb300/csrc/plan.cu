@@ -62,7 +62,6 @@ struct DimTables {
   int d;
   int N[kMaxDim], K[kMaxDim], J[kMaxDim];
   int64_t s_off[kMaxDim];     // into s (float) and s64 (double)
-  int64_t tw_off[kMaxDim];
   int64_t T_off[kMaxDim];     // into Tinv (double2), J*J each
 };
 
@@ -82,8 +81,8 @@ __device__ double kb_recip_ft(double t, int J, int K) {
   return 1.0 / ft;
 }
 
-// One CTA per dimension: scaling factors (max-normalised) and twiddles.
-__global__ void k_scaling_twiddle(DimTables D, float* s, double* s64, float2* tw) {
+// One CTA per dimension: scaling factors (max-normalised).
+__global__ void k_scaling(DimTables D, float* s, double* s64) {
   const int a = blockIdx.x;
   const int N = D.N[a], K = D.K[a], J = D.J[a];
   __shared__ double red[256];
@@ -104,11 +103,6 @@ __global__ void k_scaling_twiddle(DimTables D, float* s, double* s64, float2* tw
     const double v = s64[D.s_off[a] + n] / smax;
     s64[D.s_off[a] + n] = v;
     s[D.s_off[a] + n] = (float)v;
-  }
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    double sn, cs;
-    sincospi(-2.0 * (double)k / (double)K, &sn, &cs);
-    tw[D.tw_off[a] + k] = make_float2((float)cs, (float)sn);
   }
 }
 
@@ -570,7 +564,7 @@ cudaError_t dalloc(nufft_plan_t* p, T** ptr, int64_t count) {
 }
 
 void free_plan_memory(nufft_plan_t* p) {
-  void* bufs[] = {p->s, p->twiddle, p->kf, p->coef, p->perm, p->bin_start, p->chunks, p->bin_chunk,
+  void* bufs[] = {p->s, p->kf, p->coef, p->perm, p->bin_start, p->chunks, p->bin_chunk,
                   p->tiles, p->grid, p->ytmp, p->x_stage, p->y_stage, p->solver_ws, p->kspace_ws, p->mbuf,
                   p->s64, p->Tinv, p->om_sorted, p->dcoef, p->bgrid, p->btiles, p->bytmp, p->bimg,
                   p->cheb, p->sort_keys, p->sort_vals, p->sort_hist, p->perm2, p->flags, p->cmax};
@@ -584,7 +578,7 @@ DimTables dim_tables(const nufft_plan_t* p) {
   D.d = p->g.d;
   for (int a = 0; a < p->g.d; ++a) {
     D.N[a] = p->g.N[a]; D.K[a] = p->g.K[a]; D.J[a] = p->g.J[a];
-    D.s_off[a] = p->s_off[a]; D.tw_off[a] = p->tw_off[a]; D.T_off[a] = p->T_off[a];
+    D.s_off[a] = p->s_off[a]; D.T_off[a] = p->T_off[a];
   }
   return D;
 }
@@ -745,17 +739,16 @@ int build_plan(nufft_plan_t* p, const float* om) {
   if (rc != NUFFT_OK) return rc;
 
   // ---- per-dimension tables
-  int64_t s_tot = 0, tw_tot = 0, T_tot = 0;
+  int64_t s_tot = 0, T_tot = 0;
   for (int a = 0; a < d; ++a) {
-    p->s_off[a] = s_tot; p->tw_off[a] = tw_tot; p->T_off[a] = T_tot;
-    s_tot += g.N[a]; tw_tot += g.K[a]; T_tot += (int64_t)g.J[a] * g.J[a];
+    p->s_off[a] = s_tot; p->T_off[a] = T_tot;
+    s_tot += g.N[a]; T_tot += (int64_t)g.J[a] * g.J[a];
   }
   const DimTables D = dim_tables(p);
   NUFFT_CUDA_TRY(p, dalloc(p, &p->s, s_tot));
-  NUFFT_CUDA_TRY(p, dalloc(p, &p->twiddle, tw_tot));
   NUFFT_CUDA_TRY(p, dalloc(p, &p->s64, s_tot));
   NUFFT_CUDA_TRY(p, dalloc(p, &p->Tinv, T_tot));
-  k_scaling_twiddle<<<d, 256, 0, st>>>(D, p->s, p->s64, p->twiddle);
+  k_scaling<<<d, 256, 0, st>>>(D, p->s, p->s64);
   NUFFT_CUDA_TRY(p, cudaGetLastError());
   k_minmax_T<<<d, 256, 0, st>>>(D, p->s64, p->Tinv, p->flags + 1);
   NUFFT_CUDA_TRY(p, cudaGetLastError());
@@ -821,7 +814,7 @@ int ensure_coef_derivatives(nufft_plan_t* p) {
   D.d = p->g.d;
   for (int a = 0; a < p->g.d; ++a) {
     D.N[a] = p->g.N[a]; D.K[a] = p->g.K[a]; D.J[a] = p->g.J[a];
-    D.s_off[a] = p->s_off[a]; D.tw_off[a] = p->tw_off[a]; D.T_off[a] = p->T_off[a];
+    D.s_off[a] = p->s_off[a]; D.T_off[a] = p->T_off[a];
   }
   const int64_t n = p->M * p->g.d;
   k_coefficients<<<(unsigned)((n + 127) / 128), 128, 0, p->stream>>>(
