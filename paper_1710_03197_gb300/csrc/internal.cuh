@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <initializer_list>
 
 #include "../../include/nufft_gb300.h"
@@ -124,6 +125,8 @@ struct nufft_plan {
   uint32_t* cmax;           // [kMaxDim] largest |coefficient| per dimension (float bits), for the gridding scale
   int64_t chunk_cap;
   uint64_t generation;      // bumped whenever recorded graphs may be stale (drop_graphs)
+  int4* red_work;           // [nbins] 2D tile-reduction work list of a single transform (plan.cu)
+  int red_ctas;             // its items (0: no list; the one-tile-per-CTA reduction runs)
 
 
   // Toeplitz-embedded normal operator (nufft_toeplitz_init)
@@ -168,6 +171,13 @@ cudaError_t dev_free(void* ptr);
 template <class T>
 inline cudaError_t dev_malloc(T** ptr, size_t bytes) {
   return dev_malloc_bytes(reinterpret_cast<void**>(ptr), bytes);
+}
+
+// Group size and thread groups of the 2D tile reduction of one transform
+// (tiles of `cells` cells); shared by the launcher and the plan's work list.
+inline void reduce2d_groups(int cells, int* gsize, int* ng) {
+  *gsize = std::max(32, std::min(1024, (cells + 127) / 128 * 32));
+  *ng = std::max(1, std::min(4, 1024 / *gsize));
 }
 
 // ------------------------------------------------------------------ launchers

@@ -662,6 +662,47 @@ __host__ __device__ constexpr uint64_t subset_masks() {
   return t;
 }
 
+// Per-cell set-up of a tile reduction: the thread's CPT cells are
+// cbase + tg + k * gsize of tile bc (coordinates in tiles); loc0 is a cell's
+// offset in a padded tile, emask the neighbours e whose padded tiles reach it
+// (0 beyond cend), goff its grid offset.
+template <int D, int CPT, int TF>
+__device__ __forceinline__ void reduce_cells(const Geom& g, const int (&bc)[kMaxDim], int cbase, int tg, int gsize,
+                                             int tile_cells, int cend, int (&loc0)[CPT], unsigned (&emask)[CPT],
+                                             int (&goff)[CPT]) {
+  const int P1 = D > 1 ? g.P[1] : 1, P2 = D > 2 ? g.P[2] : 1;
+  // TF > 0: every tile edge is TF, so the cell decompositions below divide by constants
+  const int T1 = D > 1 ? (TF > 0 ? TF : g.T[1]) : 1, T2 = D > 2 ? (TF > 0 ? TF : g.T[2]) : 1;
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int c = min(cbase + tg + k * gsize, tile_cells - 1);
+    int lc[3] = {0, 0, 0};
+    if (D == 1) {
+      lc[0] = c;
+    } else if (D == 2) {
+      lc[1] = c % T1;
+      lc[0] = c / T1;
+    } else {
+      lc[2] = c % T2;
+      lc[1] = (c / T2) % T1;
+      lc[0] = c / (T2 * T1);
+    }
+    loc0[k] = D == 1 ? lc[0] : (D == 2 ? lc[0] * P1 + lc[1] : (lc[0] * P1 + lc[1]) * P2 + lc[2]);
+    // neighbour e reaches the cell iff every axis a with e_a = 1 has the cell
+    // within J - 1 of the tile's low edge; with those axes as the bits of
+    // `near` (e's bit order), the mask is the set of subsets of near
+    unsigned near = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) near |= (lc[a] + g.T[a] < g.P[a] ? 1u : 0u) << (D - 1 - a);
+    const unsigned m = (unsigned)(subset_masks<D>() >> ((1 << D) * near)) & ((1u << (1 << D)) - 1u);
+    emask[k] = (cbase + tg + k * gsize < cend) ? m : 0u;
+    int off = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) off += (bc[a] * g.T[a] + lc[a]) * (int)g.Kstride[a];
+    goff[k] = off;
+  }
+}
+
 template <int D, int CPT, bool COHERENT, int TF>
 __device__ __forceinline__ void reduce_tile(const float2* __restrict__ tiles, const int32_t* __restrict__ bin_chunk,
                                             float2* __restrict__ grid, const Geom& g, const int NG, const int bin,
@@ -693,8 +734,6 @@ __device__ __forceinline__ void reduce_tile(const float2* __restrict__ tiles, co
     s_delta[e] = delta;
   }
   __syncthreads();
-  // TF > 0: every tile edge is TF, so the cell decompositions below divide by constants
-  const int T1 = D > 1 ? (TF > 0 ? TF : g.T[1]) : 1, T2 = D > 2 ? (TF > 0 ? TF : g.T[2]) : 1;
   int loc0[CPT];
   unsigned emask[CPT];
   int goff[CPT];
@@ -712,34 +751,8 @@ __device__ __forceinline__ void reduce_tile(const float2* __restrict__ tiles, co
   const bool active = h < NGe;
   const int cend = min(tile_cells, cbase + gsize * CPT);
 #pragma unroll
-  for (int k = 0; k < CPT; ++k) {
-    acc[k] = make_float2(0.f, 0.f);
-    const int c = min(cbase + tg + k * gsize, tile_cells - 1);
-    int lc[3] = {0, 0, 0};
-    if (D == 1) {
-      lc[0] = c;
-    } else if (D == 2) {
-      lc[1] = c % T1;
-      lc[0] = c / T1;
-    } else {
-      lc[2] = c % T2;
-      lc[1] = (c / T2) % T1;
-      lc[0] = c / (T2 * T1);
-    }
-    loc0[k] = D == 1 ? lc[0] : (D == 2 ? lc[0] * P1 + lc[1] : (lc[0] * P1 + lc[1]) * P2 + lc[2]);
-    // neighbour e reaches the cell iff every axis a with e_a = 1 has the cell
-    // within J - 1 of the tile's low edge; with those axes as the bits of
-    // `near` (e's bit order), the mask is the set of subsets of near
-    unsigned near = 0;
-#pragma unroll
-    for (int a = 0; a < D; ++a) near |= (lc[a] + g.T[a] < g.P[a] ? 1u : 0u) << (D - 1 - a);
-    const unsigned m = (unsigned)(subset_masks<D>() >> ((1 << D) * near)) & ((1u << (1 << D)) - 1u);
-    emask[k] = (cbase + tg + k * gsize < cend) ? m : 0u;
-    int off = 0;
-#pragma unroll
-    for (int a = 0; a < D; ++a) off += (bc[a] * g.T[a] + lc[a]) * (int)g.Kstride[a];
-    goff[k] = off;
-  }
+  for (int k = 0; k < CPT; ++k) acc[k] = make_float2(0.f, 0.f);
+  reduce_cells<D, CPT, TF>(g, bc, cbase, tg, gsize, tile_cells, cend, loc0, emask, goff);
   const int64_t pc = g.padded_cells;
   if (active) {
     int idx = 0;  // running index over the (e, chunk) pairs
@@ -810,6 +823,71 @@ k_gridding_reduce(const float2* __restrict__ tiles_b, const int32_t* __restrict_
   const int cbase = (blockIdx.x - bin * slices) * (blockDim.x / NG) * CPT;
   reduce_tile<D, CPT, false, TF>(tiles_b + (int64_t)blockIdx.y * tbs, bin_chunk, grid_b + (int64_t)blockIdx.y * gbs, g,
                              NG, bin, part, cbase);
+}
+
+
+// One thread group (tg = 0 .. gsize - 1, no barriers) reduces 2D grid tile
+// `bin` on its own, in the order of reduce_tile with a single group: neighbour
+// e outer, the source bin's chunks in order, so the tile's cells are the same
+// bit for bit.  Each thread fetches the four source bins' chunk ranges itself.
+template <int CPT, int TF>
+__device__ __forceinline__ void reduce_tile_group2d(const float2* __restrict__ tiles,
+                                                    const int32_t* __restrict__ bin_chunk, float2* __restrict__ grid,
+                                                    const Geom& g, const int bin, const int tg, const int gsize) {
+  int bc[kMaxDim] = {bin / g.nb[1], bin % g.nb[1], 0};
+  int q0[4], q1[4], delta[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int e0 = e >> 1, e1 = e & 1;
+    const int src = ((bc[0] - e0 + g.nb[0]) % g.nb[0]) * g.nb[1] + (bc[1] - e1 + g.nb[1]) % g.nb[1];
+    q0[e] = __ldg(&bin_chunk[src]);
+    q1[e] = __ldg(&bin_chunk[src + 1]);
+    delta[e] = e0 * g.T[0] * g.P[1] + e1 * g.T[1];
+  }
+  const int tile_cells = TF > 0 ? TF * TF : g.T[0] * g.T[1];
+  const int cend = min(tile_cells, gsize * CPT);
+  int loc0[CPT];
+  unsigned emask[CPT];
+  int goff[CPT];
+  float2 acc[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) acc[k] = make_float2(0.f, 0.f);
+  reduce_cells<2, CPT, TF>(g, bc, 0, tg, gsize, tile_cells, cend, loc0, emask, goff);
+  const int64_t pc = g.padded_cells;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    for (int q = q0[e]; q < q1[e]; ++q) {
+      const float2* src = tiles + (int64_t)q * pc + delta[e];
+#pragma unroll
+      for (int k = 0; k < CPT; ++k)
+        if ((emask[k] >> e) & 1u) acc[k] = cadd(acc[k], __ldg(&src[loc0[k]]));
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < CPT; ++k)
+    if (tg + k * gsize < cend) grid[goff[k]] = acc[k];
+}
+
+// 2D tile reduction of a single transform over a plan-time work list: item
+// {t, -2, -1, -1} is a dense tile (more than 8 (neighbour, chunk) pairs),
+// reduced by the whole CTA as in k_gridding_reduce; any other item holds up
+// to NG sparse tiles (-1 = none), one per thread group.  Sparse tiles then
+// take a quarter of the CTAs they took one per CTA, with every group busy.
+template <int CPT, int TF>
+__global__ void __launch_bounds__(256, 3)
+k_gridding_reduce_packed2d(const float2* __restrict__ tiles, const int32_t* __restrict__ bin_chunk,
+                           float2* __restrict__ grid, const int4* __restrict__ work, const Geom g, const int NG) {
+  extern __shared__ float2 part[];
+  const int4 w = work[blockIdx.x];
+  if (w.y == -2) {   // CTA-uniform
+    reduce_tile<2, CPT, false, TF>(tiles, bin_chunk, grid, g, NG, w.x, part, 0);
+    return;
+  }
+  const int gsize = blockDim.x / NG;
+  const int h = threadIdx.x / gsize;
+  const int t = h == 0 ? w.x : (h == 1 ? w.y : (h == 2 ? w.z : w.w));
+  if (t < 0) return;
+  reduce_tile_group2d<CPT, TF>(tiles, bin_chunk, grid, g, t, threadIdx.x - h * gsize, gsize);
 }
 
 
@@ -957,6 +1035,16 @@ cudaError_t launch_reduce(const nufft_plan_t* p, const float2* tiles, float2* gr
   const size_t smem = NG > 1 ? (size_t)NG * 4 * gsize * sizeof(float2) : 0;
   bool t16 = D > 1;
   for (int a = 0; a < D; ++a) t16 = t16 && p->g.T[a] == 16;
+  if constexpr (D == 2) {
+    // a single transform with the plan's work list: sparse tiles packed NG to a CTA
+    int gs = 0, ng = 0;
+    reduce2d_groups(cells, &gs, &ng);
+    if (nb == 1 && p->red_ctas > 0 && gs == gsize && ng == NG) {
+      auto kern = t16 ? k_gridding_reduce_packed2d<4, 16> : k_gridding_reduce_packed2d<4, 0>;
+      kern<<<(unsigned)p->red_ctas, gsize * NG, smem, p->stream>>>(tiles, p->bin_chunk, grid, p->red_work, p->g, NG);
+      return cudaGetLastError();
+    }
+  }
   auto kern = t16 ? k_gridding_reduce<D, 4, (D > 1 ? 16 : 0)> : k_gridding_reduce<D, 4, 0>;
   kern<<<dim3((unsigned)(p->g.nbins * slices), (unsigned)nb), gsize * NG, smem, p->stream>>>(
       tiles, p->bin_chunk, grid, p->g, NG, p->nchunks * p->g.padded_cells, p->Kprod, slices);

@@ -567,7 +567,7 @@ void free_plan_memory(nufft_plan_t* p) {
   void* bufs[] = {p->s, p->kf, p->coef, p->perm, p->bin_start, p->chunks, p->bin_chunk,
                   p->tiles, p->grid, p->ytmp, p->x_stage, p->y_stage, p->solver_ws, p->kspace_ws, p->mbuf,
                   p->s64, p->Tinv, p->om_sorted, p->dcoef, p->bgrid, p->btiles, p->bytmp, p->bimg,
-                  p->cheb, p->sort_keys, p->sort_vals, p->sort_hist, p->perm2, p->flags, p->cmax};
+                  p->cheb, p->sort_keys, p->sort_vals, p->sort_hist, p->perm2, p->flags, p->cmax, p->red_work};
   for (void* b : bufs)
     if (b) dev_free(b);
 }
@@ -687,6 +687,43 @@ int build_points(nufft_plan_t* p, const float* om) {
     NUFFT_CUDA_TRY(p, cudaMemcpyAsync(p->chunks, ch.data(), ch.size() * sizeof(Chunk), cudaMemcpyHostToDevice, st));
   NUFFT_CUDA_TRY(p, cudaMemcpyAsync(p->bin_chunk, bc.data(), bc.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
                                     st));
+
+  // ---- 2D tile-reduction work list (single transforms): a dense tile (more
+  // than 8 (neighbour, chunk) pairs, which its thread groups split) gets a CTA
+  // of its own, {t, -2, -1, -1}; sparse tiles go NG to a CTA, one per group
+  p->red_ctas = 0;
+  if (d == 2 && nch > 0) {
+    int gsize = 0, ng = 0;
+    reduce2d_groups(g.T[0] * g.T[1], &gsize, &ng);
+    if (gsize * ng <= 256) {
+      const int nb0 = g.nb[0], nb1 = g.nb[1];
+      std::vector<int4> wl;
+      int pend[4] = {-1, -1, -1, -1}, fill = 0;
+      for (int t = 0; t < (int)g.nbins; ++t) {
+        const int b0 = t / nb1, b1 = t % nb1;
+        int npairs = 0;
+        for (int e = 0; e < 4; ++e) {
+          const int src = ((b0 - (e >> 1) + nb0) % nb0) * nb1 + (b1 - (e & 1) + nb1) % nb1;
+          npairs += bc[src + 1] - bc[src];
+        }
+        if (npairs > 8) {
+          wl.push_back(make_int4(t, -2, -1, -1));
+        } else {
+          pend[fill++] = t;
+          if (fill == ng) {
+            wl.push_back(make_int4(pend[0], pend[1], pend[2], pend[3]));
+            pend[0] = pend[1] = pend[2] = pend[3] = -1;
+            fill = 0;
+          }
+        }
+      }
+      if (fill > 0) wl.push_back(make_int4(pend[0], pend[1], pend[2], pend[3]));
+      if (!p->red_work) NUFFT_CUDA_TRY(p, dalloc(p, &p->red_work, g.nbins));
+      NUFFT_CUDA_TRY(p, cudaMemcpyAsync(p->red_work, wl.data(), wl.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+      NUFFT_CUDA_TRY(p, cudaStreamSynchronize(st));   // wl is a host temporary
+      p->red_ctas = (int)wl.size();
+    }
+  }
 
   // ---- order the points of each chunk for conflict-free shared-memory atomics
   if (M > 0 && nch > 0) {
