@@ -646,8 +646,7 @@ k_gridding_chunk(const float2* __restrict__ y_b, float2* __restrict__ tiles_b, c
 // costs one predicated load per cell.  The sum runs over e, then over the
 // source bin's chunks, in a fixed order.
 // The whole CTA reduces grid tile `bin`; `part` is shared scratch of
-// blockDim.x * CPT values.  COHERENT reads the partial tiles through L2 only,
-// for tiles written by other CTAs of the same launch.
+// blockDim.x * CPT values.
 // The cells reduced are cbase .. cbase + (blockDim/NG)*CPT - 1 of the tile (all
 // of it when cbase = 0 and the groups span it).
 // Entry n (2^D bits at bit 2^D * n) is the set of the e in [0, 2^D) with
@@ -703,7 +702,7 @@ __device__ __forceinline__ void reduce_cells(const Geom& g, const int (&bc)[kMax
   }
 }
 
-template <int D, int CPT, bool COHERENT, int TF>
+template <int D, int CPT, int TF>
 __device__ __forceinline__ void reduce_tile(const float2* __restrict__ tiles, const int32_t* __restrict__ bin_chunk,
                                             float2* __restrict__ grid, const Geom& g, const int NG, const int bin,
                                             float2* part, const int cbase = 0) {
@@ -773,7 +772,7 @@ __device__ __forceinline__ void reduce_tile(const float2* __restrict__ tiles, co
 #pragma unroll
           for (int k = 0; k < CPT; ++k) {
             const bool on = (emask[k] >> e) & 1u;
-            v[u][k] = on ? (COHERENT ? __ldcg(&src[loc0[k]]) : __ldg(&src[loc0[k]])) : make_float2(0.f, 0.f);
+            v[u][k] = on ? __ldg(&src[loc0[k]]) : make_float2(0.f, 0.f);
           }
         }
 #pragma unroll
@@ -787,7 +786,7 @@ __device__ __forceinline__ void reduce_tile(const float2* __restrict__ tiles, co
         const float2* src = tiles + (int64_t)q * pc + delta;
 #pragma unroll
         for (int k = 0; k < CPT; ++k)
-          if ((emask[k] >> e) & 1u) acc[k] = cadd(acc[k], COHERENT ? __ldcg(&src[loc0[k]]) : __ldg(&src[loc0[k]]));
+          if ((emask[k] >> e) & 1u) acc[k] = cadd(acc[k], __ldg(&src[loc0[k]]));
       }
       idx += q1 - q0;
     }
@@ -821,7 +820,7 @@ k_gridding_reduce(const float2* __restrict__ tiles_b, const int32_t* __restrict_
   extern __shared__ float2 part[];
   const int bin = blockIdx.x / slices;
   const int cbase = (blockIdx.x - bin * slices) * (blockDim.x / NG) * CPT;
-  reduce_tile<D, CPT, false, TF>(tiles_b + (int64_t)blockIdx.y * tbs, bin_chunk, grid_b + (int64_t)blockIdx.y * gbs, g,
+  reduce_tile<D, CPT, TF>(tiles_b + (int64_t)blockIdx.y * tbs, bin_chunk, grid_b + (int64_t)blockIdx.y * gbs, g,
                              NG, bin, part, cbase);
 }
 
@@ -880,7 +879,7 @@ k_gridding_reduce_packed2d(const float2* __restrict__ tiles, const int32_t* __re
   extern __shared__ float2 part[];
   const int4 w = work[blockIdx.x];
   if (w.y == -2) {   // CTA-uniform
-    reduce_tile<2, CPT, false, TF>(tiles, bin_chunk, grid, g, NG, w.x, part, 0);
+    reduce_tile<2, CPT, TF>(tiles, bin_chunk, grid, g, NG, w.x, part, 0);
     return;
   }
   const int gsize = blockDim.x / NG;
